@@ -1,0 +1,65 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake (a dropped or wrong term, a sign, an index, a transposed operand) in
+a copy of the oracle's C source, builds that copy into a scratch directory and runs the pin tests
+that should reject it.  The copy never touches the real oracle build.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sl_oracle.c")
+
+MUTATIONS = {
+    "z1_coefficient": ("1.0 - 2.5 * x2 + 1.5 * x3", "1.0 - 2.5 * x2 + 1.4 * x3", "test_oracle_basis.py"),
+    "z2_coefficient": ("(545.0 / 24.0) * x3", "(544.0 / 24.0) * x3", "test_oracle_basis.py"),
+    "hat_shape": ("return ax < 1.0 ? 1.0 - ax : 0.0;", "return ax < 1.0 ? 1.0 - ax * ax : 0.0;", "test_oracle_basis.py"),
+    "limiter_strictness": ("if (num > g->threshold * den)", "if (num >= g->threshold * den)", "test_oracle_limiter.py"),
+    "limiter_denominator": ("double den = fmax(fabs(dp), fabs(dm));", "double den = fmin(fabs(dp), fabs(dm));",
+                            "test_oracle_limiter.py"),
+    "limiter_axis": ("kp[a] += 1;", "kp[0] += 1;", "test_oracle_limiter.py"),
+    "rk4_weight": ("(k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a])", "(k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + 2.0 * k4[a])",
+                   "test_oracle_advect.py"),
+    "rk4_stage_time": ("or_velocity(g, y, t + 0.5 * dt, k3);", "or_velocity(g, y, t + dt, k3);", "test_oracle_advect.py"),
+    "rk4_stage_position": ("y[a] = X[a] + 0.5 * dt * k2[a];", "y[a] = X[a] + 0.5 * dt * k1[a];", "test_oracle_advect.py"),
+    "swirl_sign": ("u[1] = -(sy * sy) * or_sinpi(2.0 * x[0]) * ct;", "u[1] = (sy * sy) * or_sinpi(2.0 * x[0]) * ct;",
+                   "test_oracle_advect.py"),
+    "deform_amplitude": ("u[0] = 2.0 * sx * sx * s2y * s2z * ct;", "u[0] = sx * sx * s2y * s2z * ct;", "test_oracle_advect.py"),
+    "fourier_component": ("u[0] += m[1] * dpsi;", "u[0] += m[0] * dpsi;", "test_oracle_advect.py"),
+    "cospi_reduction": ("if (a <= 0.75) return sin(M_PI * (0.5 - a));", "if (a <= 0.75) return sin(M_PI * (a - 0.5));",
+                        "test_oracle_basis.py"),
+    "jacobian_sign": ("double dw = ((v >> b) & 1) ? 1.0 : -1.0;", "double dw = ((v >> b) & 1) ? 1.0 : 1.0;",
+                      "test_oracle_mapping.py"),
+    "newton_update_sign": ("xi[a] -= s[a];", "xi[a] += s[a];", "test_oracle_mapping.py"),
+    "walk_direction": ("if (xi[a] < -g->slack) c[a] -= 1;", "if (xi[a] < -g->slack) c[a] += 1;", "test_oracle_mapping.py"),
+    "vertex_displacement_sign": ("P[v * d + a] = (double)(k[a] - j[a]) + D[idx * d + a];",
+                                 "P[v * d + a] = (double)(k[a] - j[a]) - D[idx * d + a];", "test_oracle_mapping.py"),
+    "interp_argument_sign": ("wt *= or_zspline(m, (double)(c[a] - k[a]) + xi[a]);",
+                             "wt *= or_zspline(m, (double)(c[a] - k[a]) - xi[a]);", "test_oracle_remap.py"),
+    "interp_transposed_axes": ("wt *= or_zspline(m, (double)(c[a] - k[a]) + xi[a]);",
+                               "wt *= or_zspline(m, (double)(c[a] - k[a]) + xi[d - 1 - a]);", "test_oracle_remap.py"),
+    "order_stencil_offset": ("k[a] = c[a] - m + r % w;\n                r /= w;\n            }\n            if",
+                             "k[a] = c[a] - m + 1 + r % w;\n                r /= w;\n            }\n            if",
+                             "test_oracle_limiter.py"),
+    "failed_target_value": ("h_out[(int64_t)f * N + jj] = h_in[(int64_t)f * N + jj];", "h_out[(int64_t)f * N + jj] = 0.0;",
+                            "test_oracle_remap.py"),
+    "moment_centre": ("cen[a] = 0.5 * (g->lo[a] + g->hi[a]);", "cen[a] = 0.5 * (g->hi[a] - g->lo[a]);",
+                      "test_oracle_step.py"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new, test_file = MUTATIONS[name]
+    base = open(SRC).read()
+    assert old in base, "mutation pattern no longer matches the oracle source"
+    src = tmp_path / "sl_oracle.c"
+    src.write_text(base.replace(old, new, 1))
+    env = dict(os.environ, SL_ORACLE_SOURCE=str(src), SL_ORACLE_BUILD_DIR=str(tmp_path), OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join("tests", test_file)], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 1, f"planted mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
