@@ -1,0 +1,342 @@
+"""Benchmark of the forward semi-Lagrangian step (arXiv:1410.2817) on GB300.
+
+Workload: the 2-D 1024^2 periodic swirling-deformation flow (T = 5) carrying three fields
+(Gaussian sigma 0.1, a step with a circular jump of radius 0.2, sin(2pi x) sin(2pi y)), 4x4 cubic
+Z-spline stencil with limiter-driven order reduction, RK4 trajectories, dt = 5 dx (CFL 5).
+One benchmark step = one full FSL step (jump flags, RK4 trajectories, element search, Newton
+inversion, order selection, tensor Z-spline sum, reset) through sl_step on the FP32 production
+path (FP32 bulk, FP32 Newton with FP64 re-solves of near-degenerate targets).  L2 is flushed
+(a 512 MiB write) before every timed step, so each step starts cold.
+
+Metric: node-updates/s (one node-update = one grid node advanced one full step, all 3 fields).
+The plain FP64 GPU path is timed beside it ("fp64"), and the CPU oracle on a bounded sample
+("cpu_baseline").  `--impl reference` times the CPU oracle alone as the reference arm.
+
+Multi-GPU: every rank advances its own replica of the grid (independent problems, no collective);
+value = all ranks' node-updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "node-updates/s (2D 1024^2 swirl, 3 fields, one full FSL step)"
+UNIT = "node-updates/s"
+N_SIDE = 1024
+NFIELDS = 3
+FLUSH_BYTES = 512 << 20
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one tiled FP32 remap launch at 1024^2 (3 fields),
+# from the ncu capture summarised in profiles/; valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {"bytes_per_launch": None, "source_sha": None}
+
+
+def _source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1410_2817_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+        threading.Thread(target=self._reader, daemon=True).start()
+
+    def _reader(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if s[3 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist.init_process_group("nccl")
+    return dist, rank, ws, local
+
+
+def _barrier(dist, torch):
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def _max_over_ranks(dist, torch, value: float) -> float:
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(budget_s: float = 20.0, steps_max: int = 4):
+    """The oracle (as it stands) on the GPU machine's host cores: whole 1024^2 steps until the budget
+    is spent (at least one)."""
+    from oracle import oracle
+    from paper_1410_2817_gb300 import inputs
+    wl = inputs.workload_swirl(N_SIDE)
+    og = oracle.OracleGrid(dim=2, n=wl.n, nfields=NFIELDS, velocity=wl.velocity, velocity_params=wl.velocity_params)
+    h = wl.fields
+    done, t0 = 0, time.perf_counter()
+    while done < steps_max:
+        h, _ = oracle.step(og, h, wl.dt * done, wl.dt, 1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": wl.nnodes * done / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{done} full step(s) of the 1024^2 x 3-field swirl workload, FP64, OpenMP over targets",
+            "seconds": el}
+
+
+def run_reference(args):
+    dist, rank, ws, local = (None, 0, 1, 0)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    from oracle import oracle
+    from paper_1410_2817_gb300 import inputs
+    oracle.build()
+    wl = inputs.workload_swirl(N_SIDE)
+    og = oracle.OracleGrid(dim=2, n=wl.n, nfields=NFIELDS, velocity=wl.velocity, velocity_params=wl.velocity_params)
+    h = wl.fields
+    for k in range(args.warmup):
+        h, _ = oracle.step(og, h, wl.dt * k, wl.dt, 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        h, _ = oracle.step(og, h, wl.dt * (args.warmup + k), wl.dt, 1)
+    el = time.perf_counter() - t0
+    value = wl.nnodes * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "swirl2d_1024x1024_3fields", "n": N_SIDE, "fields": NFIELDS,
+                                            "cfl": 5, "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.max_threads(), "value": value, "unit": UNIT,
+                             "sample": f"{args.steps} full steps of the workload (after {args.warmup} warm-up)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    dist, rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1410_2817_gb300 import build, inputs, sl
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    sl.lib()
+    dev = torch.device("cuda", local)
+    wl = inputs.workload_swirl(N_SIDE)
+    N = wl.nnodes
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def run_path(dtype, newton, steps, warmup):
+        g = sl.grid_for(wl, dtype, newton_mode=newton)
+        td = torch.float32 if dtype == sl.SL_F32 else torch.float64
+        f = torch.tensor(wl.fields, dtype=td, device=dev)
+        s = torch.empty_like(f)
+        t = 0.0
+        for _ in range(warmup):
+            g.step(f, s, t, wl.dt, 1)
+            t += wl.dt
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        _barrier(dist, torch)
+        l0 = g.diagnostics()["kernel_launches"]
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            g.step(f, s, t, wl.dt, 1)
+            ev[k][1].record(stream)
+            t += wl.dt
+        _barrier(dist, torch)
+        wall = time.perf_counter() - w0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return g, f, s, ms, wall, t, g.diagnostics()["kernel_launches"] - l0
+
+    # ---- FP32 production path (headline) -----------------------------------------------------
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    g32, f32, s32, ms32, wall32, t_end, launches = run_path(sl.SL_F32, sl.SL_NEWTON_MIXED, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    dev_ms = sum(ms32)
+    dev_ms_max = _max_over_ranks(dist, torch, dev_ms)
+    value = ws * N * args.steps / (dev_ms_max * 1e-3)
+    diag = g32.diagnostics()
+
+    # ---- kernel-level timing of the dominant kernel (remap) for the roofline -----------------
+    g32.advect(t_end, wl.dt)
+    out = torch.empty_like(f32)
+    kms = []
+    for k in range(max(10, args.steps // 2)):
+        flush.fill_(k & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g32.remap(f32, out)
+        b.record(stream)
+        kms.append((a, b))
+    torch.cuda.synchronize()
+    remap_ms = statistics.mean(a.elapsed_time(b) for a, b in kms)
+    adv = []
+    for k in range(10):
+        flush.fill_(k & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g32.advect(t_end, wl.dt)
+        b.record(stream)
+        adv.append((a, b))
+    torch.cuda.synchronize()
+    advect_ms = statistics.mean(a.elapsed_time(b) for a, b in adv)
+    hbm, peak_kind = _peaks()
+    alg_bytes = N * (2 * 4 + 2 * NFIELDS * 4)  # D (2 x f32) + 3 fields in + 3 fields out
+    achieved = alg_bytes / (remap_ms * 1e-3) / 1e9
+    sha = _source_sha()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_sha"] == sha else None
+
+    # ---- plain FP64 GPU path ----------------------------------------------------------------
+    g64, _, _, ms64, _, _, _ = run_path(sl.SL_F64, sl.SL_NEWTON_F64, args.fp64_steps, 3)
+    fp64_value = ws * N * args.fp64_steps / (_max_over_ranks(dist, torch, sum(ms64)) * 1e-3)
+
+    # ---- end to end through the public API with host buffers ---------------------------------
+    host_in = torch.tensor(wl.fields, dtype=torch.float32).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(5, args.steps // 2)
+    t = t_end
+    _barrier(dist, torch)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(e2e_steps):
+        f32.copy_(host_in, non_blocking=True)
+        g32.step(f32, s32, t, wl.dt, 1)
+        host_out.copy_(f32, non_blocking=True)
+        t += wl.dt
+    e1.record(stream)
+    _barrier(dist, torch)
+    e2e_ms = _max_over_ranks(dist, torch, e0.elapsed_time(e1))
+    e2e_value = ws * N * e2e_steps / (e2e_ms * 1e-3)
+    plane_bytes = NFIELDS * N * 4
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "swirl2d_1024x1024_3fields", "n": N_SIDE, "fields": NFIELDS, "cfl": 5, "steps_per_call": 1,
+                   "newton": "f32 with f64 re-solve of near-degenerate targets", "max_order": 1,
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
+        "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": sum(ms64) / args.fp64_steps,
+                 "path": "plain FP64 kernels (one thread per target, global gathers)",
+                 "speedup_of_f32": value / fp64_value},
+        "roofline": {"bound": "hbm", "kernel": "remap (sl_remap_fields, FP32)", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": remap_ms, "advect_ms": advect_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": plane_bytes, "d2h_bytes_per_step": plane_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "diagnostics": {k: diag[k] for k in ("targets", "fail_locate", "fail_newton", "fail_fold", "hops_max",
+                                             "iters_max", "newton_f64", "order_hist", "tiles_fallback")},
+        "mean_hops": diag["hops_sum"] / max(1, diag["targets"]),
+        "mean_newton_iters": diag["iters_sum"] / max(1, diag["targets"]),
+        "source_sha": sha,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

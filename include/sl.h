@@ -1,0 +1,174 @@
+/*
+ * sl.h -- C ABI of libsl.so, a GB300 (sm_103a) implementation of the forward semi-Lagrangian (FSL)
+ * step of Becerra-Sagredo, Malaga & Mandujano, "Moments Preserving and high-resolution
+ * Semi-Lagrangian Advection Scheme" (arXiv:1410.2817).
+ *
+ * The library solves the transport system Dh_f/Dt = 0 (Sec. 2, eq. momento with S = 0) for
+ * `nfields` scalar fields carried by a moving material grid whose nodes follow a given velocity
+ * u(x, t) (eq. vel).  One step:
+ *   1. flags    -- jump criterion of Sec. 2.3 on the fields at the start of the step;
+ *   2. advect   -- every Lagrangian node is moved from its reference position by one classical
+ *                  RK4 step of eq. (vel);
+ *   3. remap    -- every reference node is located in the deformed grid (Sec. 2.2 element search),
+ *                  the multilinear element map (eq. mapping1, Z~0 geometry) is inverted by Newton's
+ *                  method, the interpolation order is lowered near flagged nodes (Sec. 2.3) and the
+ *                  tensor-product cardinal Z-spline sum (eq. multiZ, Appendix) gives the new value;
+ *   4. reset    -- the remapped values become the fields on the reference mesh (Sec. 2).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: periodic box [lo, hi) per axis with n[a] nodes; node i sits at lo + i*(hi-lo)/n.
+ *     A field plane is n[0]*n[1](*n[2]) contiguous values of the grid's dtype, x fastest
+ *     (index = ix + n0*(iy + n1*iz)).  Field planes are caller-owned DEVICE memory.
+ *   - Displacements D are stored in cell units (displacement / dx per axis).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is asynchronous on
+ *     that stream unless its comment says "synchronises".
+ *   - Errors: invalid arguments return SL_ERR_ARG before any work is queued; a failed CUDA call or
+ *     launch returns SL_ERR_CUDA (text via sl_last_error()).  Kernels never trap: a target whose
+ *     element search or Newton inversion fails keeps its old value and is counted in the grid's
+ *     diagnostics (read with sl_get_diagnostics); with SL_FAIL_ERROR, sl_step additionally
+ *     synchronises at its end and returns SL_ERR_LOCATE / SL_ERR_NEWTON / SL_ERR_FOLD.
+ *   - Threading: one grid is used by one stream at a time.
+ *   - The library allocates no device memory: every device buffer is either the caller's field
+ *     planes or the caller-supplied workspace given to sl_create_grid.
+ */
+#ifndef SL_H
+#define SL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SL_OK = 0,
+    SL_ERR_ARG = 1,         /* invalid argument: NULL pointer, bad size, enum or alignment      */
+    SL_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed                       */
+    SL_ERR_NOMEM = 3,       /* workspace smaller than sl_grid_workspace_bytes()                  */
+    SL_ERR_BUDGET = 4,      /* a batch does not fit the memory it was given                      */
+    SL_ERR_LOCATE = 5,      /* some target's element search gave up after walk_max hops           */
+    SL_ERR_NEWTON = 6,      /* some target's Newton inversion did not converge                    */
+    SL_ERR_FOLD = 7,        /* some target met a folded element (det J <= 0)                      */
+    SL_ERR_UNSUPPORTED = 8  /* valid but unimplemented combination of options                    */
+} sl_status;
+
+enum { SL_F64 = 0, SL_F32 = 1 };                       /* dtype of field planes and of D          */
+enum { SL_RK4 = 0 };                                   /* trajectory integrator                    */
+enum {                                                 /* analytic velocity u(x, t)               */
+    SL_VEL_UNIFORM = 0,     /* params (u, v[, w])                                                   */
+    SL_VEL_SOLID_BODY = 1,  /* params (Omega, cx, cy): u = Omega (cy - y, x - cx)      (Sec. 3.1) */
+    SL_VEL_SWIRL2D = 2,     /* params (T): u = sin^2(pi x) sin(2pi y) cos(pi t/T),
+                                           v = -sin^2(pi y) sin(2pi x) cos(pi t/T)               */
+    SL_VEL_DEFORM3D = 3,    /* params (T): u = 2 sin^2(pi x) sin(2pi y) sin(2pi z) cos(pi t/T),
+                                           v, w the cyclic permutations with amplitude -1        */
+    SL_VEL_FOURIER2D = 4,   /* params (q, [kx ky a b] * q): u = d psi/dy, v = -d psi/dx with
+                                           psi = sum a cos(2pi k.x) + b sin(2pi k.x), q <= 16    */
+    SL_VEL_FOURIER3D = 5    /* params (q, [k(3) a(3) b(3)] * q): u = curl of
+                                           A = sum a cos(2pi k.x) + b sin(2pi k.x), q <= 8       */
+};
+enum { SL_NEWTON_F64 = 0, SL_NEWTON_MIXED = 1 };       /* precision of the element-map inversion  */
+enum { SL_FAIL_KEEP = 0, SL_FAIL_ERROR = 1 };          /* what a failed target reports             */
+enum { SL_START_BACKWARD = 0, SL_START_PAPER = 1 };    /* first element of the search              */
+enum { SL_KERNEL_AUTO = 0, SL_KERNEL_GENERIC = 1, SL_KERNEL_TILED = 2 };
+
+typedef struct sl_grid sl_grid; /* opaque; host object that borrows the device workspace */
+
+typedef struct {
+    int dim;                        /* 2 or 3                                                       */
+    int64_t n[3];                   /* nodes per axis (n[2] ignored in 2-D); each >= 4               */
+    double lo[3], hi[3];            /* periodic box                                                  */
+    int nfields;                    /* 1..8 fields advected together                                 */
+    int dtype;                      /* SL_F64 or SL_F32                                              */
+    int max_order;                  /* m_max of the Z-spline: 0 (linear) or 1 (cubic)                */
+    double limiter_threshold;       /* 0.25 in the paper (Sec. 2.3); < 0 disables the limiter        */
+    int integrator;                 /* SL_RK4                                                        */
+    int velocity_kind;              /* SL_VEL_*                                                      */
+    const double *velocity_params;  /* host array, copied by sl_create_grid                          */
+    int n_velocity_params;
+    int newton_mode;                /* SL_NEWTON_F64 (any dtype) or SL_NEWTON_MIXED (SL_F32 only)    */
+    int newton_max_iter;            /* <= 0 selects 8                                                */
+    int walk_max;                   /* <= 0 selects 64                                               */
+    int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
+    int walk_start;                 /* SL_START_BACKWARD (from j - D_j) or SL_START_PAPER (Sec. 2.2) */
+    int kernel;                     /* SL_KERNEL_AUTO, SL_KERNEL_GENERIC or SL_KERNEL_TILED           */
+} sl_grid_desc;
+
+/* Counters accumulated on the device since creation or the last sl_reset_diagnostics. */
+typedef struct {
+    uint64_t targets;               /* target-node remaps performed                                  */
+    uint64_t fail_locate;           /* element search gave up                                        */
+    uint64_t fail_newton;           /* Newton hit its iteration cap inside the element               */
+    uint64_t fail_fold;             /* det J <= 0                                                    */
+    uint64_t hops_sum, hops_max;    /* element-search hops (Newton solves) per target                */
+    uint64_t iters_sum, iters_max;  /* Newton iterations per target                                  */
+    uint64_t newton_f64;            /* (mixed mode) targets re-solved in FP64                        */
+    uint64_t order_hist[3];         /* field-targets interpolated with order 0, 1, 2                 */
+    uint64_t tiles_fallback;        /* tiles whose stencil window did not fit shared memory          */
+    uint64_t kernel_launches;       /* kernels this grid's calls have launched (host-side count)    */
+} sl_diag;
+
+/* Remap debug outputs (device pointers, each may be NULL). */
+typedef struct {
+    int64_t *cell;                  /* [N] wrapped linear index of the element's lower corner, -1 = failed */
+    double *xi;                     /* [N*dim] local coordinates in the element (always FP64)        */
+    uint8_t *order;                 /* [nfields*N] order used per field (255 = failed target)        */
+    uint8_t *status;                /* [N] 0 ok, 1 locate, 2 newton, 3 fold                          */
+} sl_remap_debug;
+
+/* Bytes of device workspace a grid needs (two displacement buffers, flags, counters, reduction
+ * scratch).  Returns 0 for an invalid descriptor. */
+size_t sl_grid_workspace_bytes(const sl_grid_desc *desc);
+
+/* Create a grid (Sec. 2: reference mesh plus Lagrangian grid).  `dev_workspace` is caller-owned
+ * device memory of at least sl_grid_workspace_bytes(desc) bytes, 256-byte aligned; the grid
+ * borrows it until sl_destroy_grid.  Zeroes the counters and the displacement (synchronises). */
+sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspace, size_t ws_bytes, sl_grid **out);
+sl_status sl_destroy_grid(sl_grid *grid);
+
+/* eq. (vel): move every Lagrangian node from its reference position over [t, t+dt] with one RK4
+ * step of the grid's velocity; writes the grid's current displacement D (cell units). */
+sl_status sl_advect_nodes(sl_grid *grid, double t, double dt, void *stream);
+
+/* Sec. 2 reset / Sec. 2.2-2.3 / eq. (multiZ): with the current D, compute the jump flags of `in`,
+ * locate every reference node, invert the element map, choose the order and interpolate.
+ * `in`, `out`: host arrays of nfields device pointers; in and out must not overlap. */
+sl_status sl_remap_fields(sl_grid *grid, const void *const *in, void *const *out, void *stream);
+
+/* Same as sl_remap_fields, additionally writing per-target diagnostics (any pointer may be NULL). */
+sl_status sl_remap_fields_debug(sl_grid *grid, const void *const *in, void *const *out,
+                                const sl_remap_debug *dbg, void *stream);
+
+/* nsteps full steps (flags, advect, remap, reset) starting at time t0.  `fields`: nfields device
+ * planes, updated in place; `scratch`: nfields device planes of the same size used as the other
+ * half of a ping-pong pair (contents undefined afterwards). */
+sl_status sl_step(sl_grid *grid, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
+                  void *stream);
+
+/* Sec. 3.1: discrete moments of one field plane about the box centre c:
+ * m_0 = sum h,  m_p = sum_i h_i sum_a (x_a^i - c_a)^p for 1 <= p <= pmax (<= 7), accumulated in
+ * FP64 in a fixed order.  Writes pmax+1 doubles to host_out (synchronises). */
+sl_status sl_moments(sl_grid *grid, const void *field, int pmax, double *host_out, void *stream);
+
+/* Jump flags of Sec. 2.3 for `fields` into flags_out (device, N bytes; bit f for field f). */
+sl_status sl_compute_flags(sl_grid *grid, const void *const *fields, uint8_t *flags_out, void *stream);
+
+/* Copy a displacement (device memory, grid dtype, `stride` values per node >= dim, cell units)
+ * into / out of the grid's current D. */
+sl_status sl_set_displacement(sl_grid *grid, const void *D, int64_t stride, void *stream);
+sl_status sl_get_displacement(sl_grid *grid, void *D_out, int64_t stride, void *stream);
+
+/* Read (synchronises) or zero the device counters. */
+sl_status sl_get_diagnostics(sl_grid *grid, sl_diag *out, void *stream);
+sl_status sl_reset_diagnostics(sl_grid *grid, void *stream);
+
+const char *sl_status_string(sl_status status);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char *sl_last_error(void);
+/* Version string of the library build. */
+const char *sl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SL_H */

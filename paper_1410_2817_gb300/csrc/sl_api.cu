@@ -1,0 +1,444 @@
+// sl_api.cu -- the extern "C" entry points declared in include/sl.h: argument checks, carving of
+// the caller's workspace, and dispatch to the kernels.  The library never allocates device memory.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "sl_internal.h"
+
+static thread_local char g_last_error[512];
+
+static sl_status fail_cuda(cudaError_t e, const char *where)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return SL_ERR_CUDA;
+}
+
+static sl_status fail_arg(const char *why)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "invalid argument: %s", why);
+    return SL_ERR_ARG;
+}
+
+#define SL_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return fail_cuda(e_, where);   \
+    } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------------------------------------
+// descriptor validation
+// ------------------------------------------------------------------------------------------------
+static const char *check_desc(const sl_grid_desc *d)
+{
+    if (!d) return "descriptor is NULL";
+    if (d->dim != 2 && d->dim != 3) return "dim must be 2 or 3";
+    long long N = 1;
+    for (int a = 0; a < d->dim; ++a) {
+        if (d->n[a] < 4 || d->n[a] > (1 << 20)) return "each n[a] must be in [4, 2^20]";
+        if (!(d->hi[a] > d->lo[a])) return "hi must exceed lo on every axis";
+        N *= d->n[a];
+    }
+    if (N > (1LL << 31) - 1) return "too many nodes (limit 2^31 - 1)";
+    if (d->nfields < 1 || d->nfields > SL_MAX_FIELDS) return "nfields must be in [1, 8]";
+    if (d->dtype != SL_F64 && d->dtype != SL_F32) return "dtype must be SL_F64 or SL_F32";
+    if (d->max_order < 0 || d->max_order > 2) return "max_order must be 0, 1 or 2";
+    if (d->integrator != SL_RK4) return "integrator must be SL_RK4";
+    if (d->newton_mode != SL_NEWTON_F64 && d->newton_mode != SL_NEWTON_MIXED) return "bad newton_mode";
+    if (d->newton_mode == SL_NEWTON_MIXED && d->dtype != SL_F32) return "SL_NEWTON_MIXED needs dtype SL_F32";
+    if (d->fail_policy != SL_FAIL_KEEP && d->fail_policy != SL_FAIL_ERROR) return "bad fail_policy";
+    if (d->walk_start != SL_START_BACKWARD && d->walk_start != SL_START_PAPER) return "bad walk_start";
+    if (d->kernel < SL_KERNEL_AUTO || d->kernel > SL_KERNEL_TILED) return "bad kernel";
+    if (d->newton_max_iter > 64 || d->walk_max > 4096) return "newton_max_iter <= 64 and walk_max <= 4096";
+    const int np = d->n_velocity_params;
+    if (np < 0 || np > SL_MAX_VEL_PARAMS) return "n_velocity_params out of range";
+    if (np > 0 && !d->velocity_params) return "velocity_params is NULL";
+    const double *p = d->velocity_params;
+    switch (d->velocity_kind) {
+    case SL_VEL_UNIFORM:
+        if (np < d->dim) return "uniform velocity needs dim parameters";
+        break;
+    case SL_VEL_SOLID_BODY:
+        if (d->dim != 2 || np < 3) return "solid-body rotation is 2-D with 3 parameters";
+        break;
+    case SL_VEL_SWIRL2D:
+        if (d->dim != 2 || np < 1 || !(p[0] != 0.0)) return "swirl is 2-D with a nonzero period";
+        break;
+    case SL_VEL_DEFORM3D:
+        if (d->dim != 3 || np < 1 || !(p[0] != 0.0)) return "3-D deformation is 3-D with a nonzero period";
+        break;
+    case SL_VEL_FOURIER2D: {
+        if (d->dim != 2 || np < 1) return "fourier2d is 2-D";
+        const int q = (int)p[0];
+        if ((double)q != p[0] || q < 1 || q > 16 || np < 1 + 4 * q) return "fourier2d needs 1..16 modes of 4 values";
+        break;
+    }
+    case SL_VEL_FOURIER3D: {
+        if (d->dim != 3 || np < 1) return "fourier3d is 3-D";
+        const int q = (int)p[0];
+        if ((double)q != p[0] || q < 1 || q > 8 || np < 1 + 9 * q) return "fourier3d needs 1..8 modes of 9 values";
+        break;
+    }
+    default:
+        return "unknown velocity_kind";
+    }
+    for (int q = 0; q < np; ++q)
+        if (!isfinite(p[q])) return "velocity parameters must be finite";
+    return nullptr;
+}
+
+struct Layout {
+    size_t counters, partials, moment_out, flags, D0, D1, total;
+};
+
+static Layout layout_of(const sl_grid_desc *d)
+{
+    Layout L;
+    long long N = 1;
+    for (int a = 0; a < d->dim; ++a) N *= d->n[a];
+    const size_t ts = d->dtype == SL_F64 ? 8 : 4;
+    const size_t ds = d->dim == 2 ? 2 : 4;
+    size_t off = 0;
+    L.counters = off;
+    off += align256(sizeof(DevCounters));
+    L.partials = off;
+    off += align256(sizeof(double) * 8 * SL_MOMENT_BLOCKS);
+    L.moment_out = off;
+    off += align256(sizeof(double) * 8);
+    L.flags = off;
+    off += align256((size_t)N);
+    L.D0 = off;
+    off += align256((size_t)N * ds * ts);
+    L.D1 = off;
+    off += align256((size_t)N * ds * ts);
+    L.total = off;
+    return L;
+}
+
+extern "C" size_t sl_grid_workspace_bytes(const sl_grid_desc *desc)
+{
+    if (check_desc(desc)) return 0;
+    return layout_of(desc).total;
+}
+
+extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspace, size_t ws_bytes, sl_grid **out)
+{
+    if (!out) return fail_arg("out is NULL");
+    *out = nullptr;
+    if (const char *why = check_desc(desc)) return fail_arg(why);
+    if (!dev_workspace) return fail_arg("workspace is NULL");
+    if (((uintptr_t)dev_workspace & 255u) != 0) return fail_arg("workspace must be 256-byte aligned");
+    const Layout L = layout_of(desc);
+    if (ws_bytes < L.total) {
+        snprintf(g_last_error, sizeof(g_last_error), "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+        return SL_ERR_NOMEM;
+    }
+    sl_grid *g = (sl_grid *)calloc(1, sizeof(sl_grid));
+    if (!g) return fail_arg("host allocation of the grid object failed");
+    g->desc = *desc;
+    memset(g->vel_params, 0, sizeof(g->vel_params));
+    for (int q = 0; q < desc->n_velocity_params; ++q) g->vel_params[q] = desc->velocity_params[q];
+    g->desc.velocity_params = g->vel_params;
+    if (g->desc.newton_max_iter <= 0) g->desc.newton_max_iter = 8;
+    if (g->desc.walk_max <= 0) g->desc.walk_max = 64;
+    g->dim = desc->dim;
+    g->nfields = desc->nfields;
+    g->dtype = desc->dtype;
+    g->ds = desc->dim == 2 ? 2 : 4;
+    g->tsize = desc->dtype == SL_F64 ? 8 : 4;
+    g->N = 1;
+    for (int a = 0; a < 3; ++a) {
+        g->n[a] = a < desc->dim ? desc->n[a] : 1;
+        g->N *= g->n[a];
+        g->dx[a] = a < desc->dim ? (desc->hi[a] - desc->lo[a]) / (double)desc->n[a] : 1.0;
+    }
+    g->ws = (char *)dev_workspace;
+    g->ws_bytes = ws_bytes;
+    g->counters = (DevCounters *)(g->ws + L.counters);
+    g->partials = (double *)(g->ws + L.partials);
+    g->moment_out = (double *)(g->ws + L.moment_out);
+    g->flags = (uint8_t *)(g->ws + L.flags);
+    g->D[0] = g->ws + L.D0;
+    g->D[1] = g->ws + L.D1;
+    g->dcur = 0;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ws, 0, L.total, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        free(g);
+        return fail_cuda(e, "sl_create_grid");
+    }
+    *out = g;
+    return SL_OK;
+}
+
+extern "C" sl_status sl_destroy_grid(sl_grid *grid)
+{
+    if (!grid) return fail_arg("grid is NULL");
+    free(grid);
+    return SL_OK;
+}
+
+static sl_status check_planes(const sl_grid *g, const void *const *p, const char *what)
+{
+    if (!p) return fail_arg(what);
+    for (int q = 0; q < g->nfields; ++q) {
+        if (!p[q]) return fail_arg(what);
+        if (((uintptr_t)p[q] % g->tsize) != 0) return fail_arg("field plane is not aligned to its dtype");
+    }
+    return SL_OK;
+}
+
+template <typename T>
+static bool use_tiled(const sl_grid *g)
+{
+    if (g->desc.kernel == SL_KERNEL_GENERIC) return false;
+    if (g->desc.kernel == SL_KERNEL_AUTO && g->dtype != SL_F32) return false;  // AUTO: tiled serves FP32
+    return Launch<T>::tiled_supported(g);
+}
+
+// count launches: every launcher below starts exactly `k` kernels when it succeeds
+static cudaError_t counted(sl_grid *g, cudaError_t e, int k)
+{
+    if (e == cudaSuccess) g->launches += (unsigned long long)k;
+    return e;
+}
+
+extern "C" sl_status sl_advect_nodes(sl_grid *g, double t, double dt, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (!isfinite(t) || !isfinite(dt)) return fail_arg("t and dt must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = g->dtype == SL_F64 ? Launch<double>::advect(g, g->D[g->dcur], t, dt, s)
+                                       : Launch<float>::advect(g, g->D[g->dcur], t, dt, s);
+    e = counted(g, e, 1);
+    return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_advect_nodes");
+}
+
+template <typename T>
+static cudaError_t remap_impl(sl_grid *g, const void *D, const void *const *in, void *const *out,
+                              const sl_remap_debug *dbg, cudaStream_t s)
+{
+    if (!dbg && use_tiled<T>(g)) return counted(g, Launch<T>::remap_tiled(g, D, in, out, s), 1);
+    cudaError_t e = counted(g, Launch<T>::flags(g, in, g->flags, s), 1);
+    if (e != cudaSuccess) return e;
+    return counted(g, Launch<T>::remap_generic(g, D, g->flags, in, out, dbg, s), 1);
+}
+
+static sl_status remap_entry(sl_grid *g, const void *const *in, void *const *out, const sl_remap_debug *dbg,
+                             void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (sl_status st = check_planes(g, in, "input planes")) return st;
+    if (sl_status st = check_planes(g, (const void *const *)out, "output planes")) return st;
+    for (int q = 0; q < g->nfields; ++q)
+        for (int r = 0; r < g->nfields; ++r)
+            if (in[q] == out[r]) return fail_arg("input and output planes must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *D = g->D[g->dcur];
+    cudaError_t e = g->dtype == SL_F64 ? remap_impl<double>(g, D, in, out, dbg, s)
+                                       : remap_impl<float>(g, D, in, out, dbg, s);
+    return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_remap_fields");
+}
+
+extern "C" sl_status sl_remap_fields(sl_grid *g, const void *const *in, void *const *out, void *stream)
+{
+    return remap_entry(g, in, out, nullptr, stream);
+}
+
+extern "C" sl_status sl_remap_fields_debug(sl_grid *g, const void *const *in, void *const *out,
+                                           const sl_remap_debug *dbg, void *stream)
+{
+    if (!dbg) return fail_arg("debug block is NULL");
+    return remap_entry(g, in, out, dbg, stream);
+}
+
+static sl_status read_counters(sl_grid *g, DevCounters *c, cudaStream_t s)
+{
+    SL_CUDA(cudaMemcpyAsync(c, g->counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, s), "read counters");
+    SL_CUDA(cudaStreamSynchronize(s), "read counters");
+    return SL_OK;
+}
+
+template <typename T>
+static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
+                             cudaStream_t s)
+{
+    const void *cur[SL_MAX_FIELDS];
+    void *nxt[SL_MAX_FIELDS];
+    for (int q = 0; q < g->nfields; ++q) {
+        cur[q] = fields[q];
+        nxt[q] = scratch[q];
+    }
+    cudaError_t e = cudaSuccess;
+    const bool fused = use_tiled<T>(g);
+    if (fused) {
+        // the velocity is given, so D of the next step does not depend on the fields: each fused
+        // launch remaps with D[cur] and writes D[next] for its own nodes
+        e = counted(g, Launch<T>::advect(g, g->D[g->dcur], t0, dt, s), 1);
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        const double t = t0 + (double)k * dt;
+        if (fused) {
+            const int nx = g->dcur ^ 1;
+            e = counted(g, Launch<T>::step_fused(g, g->D[g->dcur], k + 1 < nsteps ? g->D[nx] : nullptr, t + dt, dt,
+                                                 cur, nxt, s), 1);
+            if (e != cudaSuccess) return e;
+            if (k + 1 < nsteps) g->dcur = nx;
+        } else {
+            e = counted(g, Launch<T>::flags(g, cur, g->flags, s), 1);
+            if (e == cudaSuccess) e = counted(g, Launch<T>::advect(g, g->D[g->dcur], t, dt, s), 1);
+            if (e == cudaSuccess)
+                e = counted(g, Launch<T>::remap_generic(g, g->D[g->dcur], g->flags, cur, nxt, nullptr, s), 1);
+            if (e != cudaSuccess) return e;
+        }
+        for (int q = 0; q < g->nfields; ++q) {
+            void *tmp = nxt[q];
+            nxt[q] = (void *)cur[q];
+            cur[q] = tmp;
+        }
+    }
+    if (nsteps % 2 == 1) {
+        const size_t bytes = (size_t)g->N * g->tsize;
+        for (int q = 0; q < g->nfields; ++q) {
+            e = cudaMemcpyAsync(fields[q], cur[q], bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+extern "C" sl_status sl_step(sl_grid *g, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
+                             void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (sl_status st = check_planes(g, (const void *const *)fields, "field planes")) return st;
+    if (sl_status st = check_planes(g, (const void *const *)scratch, "scratch planes")) return st;
+    for (int q = 0; q < g->nfields; ++q)
+        for (int r = 0; r < g->nfields; ++r)
+            if (fields[q] == scratch[r]) return fail_arg("field and scratch planes must not overlap");
+    if (nsteps < 0) return fail_arg("nsteps must be >= 0");
+    if (!isfinite(t0) || !isfinite(dt)) return fail_arg("t0 and dt must be finite");
+    if (nsteps == 0) return SL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevCounters before;
+    if (g->desc.fail_policy == SL_FAIL_ERROR)
+        if (sl_status st = read_counters(g, &before, s)) return st;
+    cudaError_t e = g->dtype == SL_F64 ? step_impl<double>(g, fields, scratch, t0, dt, nsteps, s)
+                                       : step_impl<float>(g, fields, scratch, t0, dt, nsteps, s);
+    if (e != cudaSuccess) return fail_cuda(e, "sl_step");
+    if (g->desc.fail_policy == SL_FAIL_ERROR) {
+        DevCounters after;
+        if (sl_status st = read_counters(g, &after, s)) return st;
+        if (after.fail_locate > before.fail_locate) return SL_ERR_LOCATE;
+        if (after.fail_newton > before.fail_newton) return SL_ERR_NEWTON;
+        if (after.fail_fold > before.fail_fold) return SL_ERR_FOLD;
+    }
+    return SL_OK;
+}
+
+extern "C" sl_status sl_moments(sl_grid *g, const void *field, int pmax, double *host_out, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (!field || !host_out) return fail_arg("field or host_out is NULL");
+    if (pmax < 0 || pmax > 7) return fail_arg("pmax must be in [0, 7]");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = g->dtype == SL_F64 ? Launch<double>::moments(g, field, pmax, s)
+                                       : Launch<float>::moments(g, field, pmax, s);
+    e = counted(g, e, 2);
+    if (e != cudaSuccess) return fail_cuda(e, "sl_moments");
+    SL_CUDA(cudaMemcpyAsync(host_out, g->moment_out, sizeof(double) * (pmax + 1), cudaMemcpyDeviceToHost, s),
+            "sl_moments");
+    SL_CUDA(cudaStreamSynchronize(s), "sl_moments");
+    return SL_OK;
+}
+
+extern "C" sl_status sl_compute_flags(sl_grid *g, const void *const *fields, uint8_t *flags_out, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (sl_status st = check_planes(g, fields, "field planes")) return st;
+    if (!flags_out) return fail_arg("flags_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = g->dtype == SL_F64 ? Launch<double>::flags(g, fields, flags_out, s)
+                                       : Launch<float>::flags(g, fields, flags_out, s);
+    e = counted(g, e, 1);
+    return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_compute_flags");
+}
+
+extern "C" sl_status sl_set_displacement(sl_grid *g, const void *D, int64_t stride, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (!D) return fail_arg("D is NULL");
+    if (stride < g->dim || stride > 64) return fail_arg("stride must be in [dim, 64]");
+    if (((uintptr_t)D % g->tsize) != 0) return fail_arg("D is not aligned to its dtype");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = g->dtype == SL_F64 ? Launch<double>::copy_disp(g, D, stride, g->D[g->dcur], g->ds, s)
+                                       : Launch<float>::copy_disp(g, D, stride, g->D[g->dcur], g->ds, s);
+    e = counted(g, e, 1);
+    return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_set_displacement");
+}
+
+extern "C" sl_status sl_get_displacement(sl_grid *g, void *D_out, int64_t stride, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (!D_out) return fail_arg("D_out is NULL");
+    if (stride < g->dim || stride > 64) return fail_arg("stride must be in [dim, 64]");
+    if (((uintptr_t)D_out % g->tsize) != 0) return fail_arg("D_out is not aligned to its dtype");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = g->dtype == SL_F64 ? Launch<double>::copy_disp(g, g->D[g->dcur], g->ds, D_out, stride, s)
+                                       : Launch<float>::copy_disp(g, g->D[g->dcur], g->ds, D_out, stride, s);
+    e = counted(g, e, 1);
+    return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_get_displacement");
+}
+
+extern "C" sl_status sl_get_diagnostics(sl_grid *g, sl_diag *out, void *stream)
+{
+    if (!g || !out) return fail_arg("grid or out is NULL");
+    DevCounters c;
+    if (sl_status st = read_counters(g, &c, (cudaStream_t)stream)) return st;
+    out->targets = c.targets;
+    out->fail_locate = c.fail_locate;
+    out->fail_newton = c.fail_newton;
+    out->fail_fold = c.fail_fold;
+    out->hops_sum = c.hops_sum;
+    out->hops_max = c.hops_max;
+    out->iters_sum = c.iters_sum;
+    out->iters_max = c.iters_max;
+    out->newton_f64 = c.newton_f64;
+    for (int q = 0; q < 3; ++q) out->order_hist[q] = c.order_hist[q];
+    out->tiles_fallback = c.tiles_fallback;
+    out->kernel_launches = g->launches;
+    return SL_OK;
+}
+
+extern "C" sl_status sl_reset_diagnostics(sl_grid *g, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    SL_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(DevCounters), (cudaStream_t)stream), "sl_reset_diagnostics");
+    return SL_OK;
+}
+
+extern "C" const char *sl_status_string(sl_status st)
+{
+    switch (st) {
+    case SL_OK: return "ok";
+    case SL_ERR_ARG: return "invalid argument";
+    case SL_ERR_CUDA: return "CUDA error";
+    case SL_ERR_NOMEM: return "workspace too small";
+    case SL_ERR_BUDGET: return "memory budget exceeded";
+    case SL_ERR_LOCATE: return "element search gave up";
+    case SL_ERR_NEWTON: return "Newton inversion did not converge";
+    case SL_ERR_FOLD: return "folded element";
+    case SL_ERR_UNSUPPORTED: return "unsupported option combination";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *sl_last_error(void) { return g_last_error; }
+
+extern "C" const char *sl_version(void) { return "libsl 0.1 (sm_103a)"; }

@@ -1,0 +1,377 @@
+// sl_device.cuh -- device-side building blocks of the FSL step (arXiv:1410.2817), shared by the
+// kernels of libsl.so.  Everything is templated on the arithmetic type T (double or float) and on
+// the dimension DIM (2 or 3).
+//
+//   velocity / rk4_cells     eq. (vel): analytic velocities and one classical RK4 step
+//   newton_solve             Sec. 2.2, eq. (mapping1): inversion of the Z~0 (multilinear) map
+//   zspline / zs_weights     Appendix: cardinal Z-spline basis Z~0 (hat), Z~1, Z~2
+//   jump test                Sec. 2.3: |h+ - 2h + h-| > thr * max(|h+ - h|, |h - h-|)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/sl.h"
+
+#define SL_MAX_FIELDS 8
+#define SL_MAX_VEL_PARAMS 80
+
+// ------------------------------------------------------------------------------------------------
+// argument blocks (passed by value)
+// ------------------------------------------------------------------------------------------------
+struct DevCounters {
+    unsigned long long targets, fail_locate, fail_newton, fail_fold;
+    unsigned long long hops_sum, hops_max, iters_sum, iters_max;
+    unsigned long long newton_f64, order_hist[3], tiles_fallback;
+};
+
+template <typename T>
+struct VelArgs {
+    int kind;
+    int nmodes;
+    T p[SL_MAX_VEL_PARAMS];
+    T ct[3];          // cos(pi t/T) at the RK4 stage times t, t + dt/2, t + dt (time-dependent flows)
+    T lo[3], dx[3], inv_dx[3];
+    T dt;
+};
+
+template <typename T>
+struct GridArgs {
+    int n[3];
+    long long N;
+    int nfields;
+    int max_order;
+    T threshold;
+    int newton_max_iter;
+    int walk_max;
+    int walk_start;
+    T tol;    // Newton stop rule on max |dxi|
+    T slack;  // face tolerance of the element test
+};
+
+enum { ST_OK = 0, ST_LOCATE = 1, ST_NEWTON = 2, ST_FOLD = 3 };
+
+// ------------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_idx(int k, int n)
+{
+    int r = k % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
+
+template <typename T>
+__device__ __forceinline__ T floor_t(T x);
+template <>
+__device__ __forceinline__ double floor_t<double>(double x) { return floor(x); }
+template <>
+__device__ __forceinline__ float floor_t<float>(float x) { return floorf(x); }
+
+// ------------------------------------------------------------------------------------------------
+// eq. (vel): velocity fields of the workloads at an unwrapped physical position
+// ------------------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__device__ __forceinline__ void velocity(const VelArgs<T> &v, const T x[3], int stage, T u[3])
+{
+    const T two = T(2);
+    u[0] = u[1] = u[2] = T(0);
+    switch (v.kind) {
+    case SL_VEL_UNIFORM:
+        for (int a = 0; a < DIM; ++a) u[a] = v.p[a];
+        break;
+    case SL_VEL_SOLID_BODY:
+        u[0] = v.p[0] * (v.p[2] - x[1]);
+        u[1] = v.p[0] * (x[0] - v.p[1]);
+        break;
+    case SL_VEL_SWIRL2D: {
+        T sx, cx, sy, cy;
+        sincospi_t(x[0], &sx, &cx);
+        sincospi_t(x[1], &sy, &cy);
+        const T ct = v.ct[stage];
+        u[0] = sx * sx * (two * sy * cy) * ct;   // sin(2 pi y) = 2 sin(pi y) cos(pi y)
+        u[1] = -(sy * sy) * (two * sx * cx) * ct;
+        break;
+    }
+    case SL_VEL_DEFORM3D: {
+        T sx, cx, sy, cy, sz, cz;
+        sincospi_t(x[0], &sx, &cx);
+        sincospi_t(x[1], &sy, &cy);
+        sincospi_t(x[2], &sz, &cz);
+        const T ct = v.ct[stage];
+        const T s2x = two * sx * cx, s2y = two * sy * cy, s2z = two * sz * cz;
+        u[0] = two * sx * sx * s2y * s2z * ct;
+        u[1] = -(sy * sy) * s2z * s2x * ct;
+        u[2] = -(sz * sz) * s2x * s2y * ct;
+        break;
+    }
+    case SL_VEL_FOURIER2D: {
+        const T twopi = T(6.283185307179586476925286766559);
+        for (int q = 0; q < v.nmodes; ++q) {
+            const T *m = v.p + 1 + 4 * q;
+            T s, c;
+            sincospi_t(two * (m[0] * x[0] + m[1] * x[1]), &s, &c);
+            const T dpsi = twopi * (m[3] * c - m[2] * s);
+            u[0] += m[1] * dpsi;
+            u[1] -= m[0] * dpsi;
+        }
+        break;
+    }
+    case SL_VEL_FOURIER3D: {
+        const T twopi = T(6.283185307179586476925286766559);
+        for (int q = 0; q < v.nmodes; ++q) {
+            const T *m = v.p + 1 + 9 * q;
+            T s, c;
+            sincospi_t(two * (m[0] * x[0] + m[1] * x[1] + m[2] * x[2]), &s, &c);
+            // k x b and k x a
+            const T kb0 = m[1] * m[8] - m[2] * m[7], kb1 = m[2] * m[6] - m[0] * m[8], kb2 = m[0] * m[7] - m[1] * m[6];
+            const T ka0 = m[1] * m[5] - m[2] * m[4], ka1 = m[2] * m[3] - m[0] * m[5], ka2 = m[0] * m[4] - m[1] * m[3];
+            u[0] += twopi * (c * kb0 - s * ka0);
+            u[1] += twopi * (c * kb1 - s * ka1);
+            u[2] += twopi * (c * kb2 - s * ka2);
+        }
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// One classical RK4 step of eq. (vel) from the reference position X over [t, t + dt]; returns the
+// displacement in cell units.
+template <typename T, int DIM>
+__device__ __forceinline__ void rk4_cells(const VelArgs<T> &v, const T X[3], T out[3])
+{
+    T k1[3], k2[3], k3[3], k4[3], y[3] = {T(0), T(0), T(0)};
+    const T h = v.dt, hh = T(0.5) * v.dt;
+    velocity<T, DIM>(v, X, 0, k1);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) y[a] = X[a] + hh * k1[a];
+    velocity<T, DIM>(v, y, 1, k2);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) y[a] = X[a] + hh * k2[a];
+    velocity<T, DIM>(v, y, 1, k3);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) y[a] = X[a] + h * k3[a];
+    velocity<T, DIM>(v, y, 2, k4);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) out[a] = (h / T(6) * (k1[a] + T(2) * k2[a] + T(2) * k3[a] + k4[a])) * v.inv_dx[a];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 2.2, eq. (mapping1): Newton inversion of the multilinear element map.
+// P[v][a]: vertex v (bit a = offset along axis a) relative to the target, cell units.  The map is
+// expanded about the lower corner: x(xi) = P0 + sum_a xi_a A_a + sum_{a<b} xi_a xi_b E_ab
+// (+ xi_0 xi_1 xi_2 G in 3-D); Newton starts from the solution of the linear part.
+// Returns ST_OK, ST_NEWTON (iteration cap) or ST_FOLD (det J <= 0); xi holds the last iterate.
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T tol, T xi[3], int *iters)
+{
+    const T ax = P[1][0] - P[0][0], ay = P[1][1] - P[0][1];
+    const T bx = P[2][0] - P[0][0], by = P[2][1] - P[0][1];
+    const T ex = P[3][0] - P[1][0] - P[2][0] + P[0][0], ey = P[3][1] - P[1][1] - P[2][1] + P[0][1];
+    const T px = P[0][0], py = P[0][1];
+    *iters = 0;
+    T det = ax * by - bx * ay;
+    if (!(det > T(0))) {
+        xi[0] = xi[1] = T(NAN);
+        return ST_FOLD;
+    }
+    T s = -(px * by - py * bx) / det;
+    T t = -(ax * py - ay * px) / det;
+    for (int it = 1; it <= max_iter; ++it) {
+        *iters = it;
+        const T j11 = ax + t * ex, j21 = ay + t * ey;
+        const T j12 = bx + s * ex, j22 = by + s * ey;
+        const T st = s * t;
+        const T fx = px + s * ax + t * bx + st * ex;
+        const T fy = py + s * ay + t * by + st * ey;
+        det = j11 * j22 - j12 * j21;
+        if (!(det > T(0))) {
+            xi[0] = s;
+            xi[1] = t;
+            return ST_FOLD;
+        }
+        const T d0 = (fx * j22 - fy * j12) / det;
+        const T d1 = (j11 * fy - j21 * fx) / det;
+        s -= d0;
+        t -= d1;
+        if (fmax(fabs(d0), fabs(d1)) <= tol) {
+            xi[0] = s;
+            xi[1] = t;
+            return ST_OK;
+        }
+    }
+    xi[0] = s;
+    xi[1] = t;
+    return ST_NEWTON;
+}
+
+template <typename T>
+__device__ __forceinline__ T det3(T a00, T a01, T a02, T a10, T a11, T a12, T a20, T a21, T a22)
+{
+    return a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
+}
+
+template <typename T>
+__device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T tol, T xi[3], int *iters)
+{
+    T A[3][3], E01[3], E02[3], E12[3], G[3], P0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        P0[a] = P[0][a];
+        A[a][0] = P[1][a] - P[0][a];
+        A[a][1] = P[2][a] - P[0][a];
+        A[a][2] = P[4][a] - P[0][a];
+        E01[a] = P[3][a] - P[1][a] - P[2][a] + P[0][a];
+        E02[a] = P[5][a] - P[1][a] - P[4][a] + P[0][a];
+        E12[a] = P[6][a] - P[2][a] - P[4][a] + P[0][a];
+        G[a] = P[7][a] - P[6][a] - P[5][a] - P[3][a] + P[1][a] + P[2][a] + P[4][a] - P[0][a];
+    }
+    *iters = 0;
+    T det = det3(A[0][0], A[0][1], A[0][2], A[1][0], A[1][1], A[1][2], A[2][0], A[2][1], A[2][2]);
+    if (!(det > T(0))) {
+        xi[0] = xi[1] = xi[2] = T(NAN);
+        return ST_FOLD;
+    }
+    T r0 = -P0[0], r1 = -P0[1], r2 = -P0[2];
+    T s0 = det3(r0, A[0][1], A[0][2], r1, A[1][1], A[1][2], r2, A[2][1], A[2][2]) / det;
+    T s1 = det3(A[0][0], r0, A[0][2], A[1][0], r1, A[1][2], A[2][0], r2, A[2][2]) / det;
+    T s2 = det3(A[0][0], A[0][1], r0, A[1][0], A[1][1], r1, A[2][0], A[2][1], r2) / det;
+    for (int it = 1; it <= max_iter; ++it) {
+        *iters = it;
+        T F[3], J[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            F[a] = P0[a] + s0 * A[a][0] + s1 * A[a][1] + s2 * A[a][2] + s0 * s1 * E01[a] + s0 * s2 * E02[a]
+                   + s1 * s2 * E12[a] + s0 * s1 * s2 * G[a];
+            J[a][0] = A[a][0] + s1 * E01[a] + s2 * E02[a] + s1 * s2 * G[a];
+            J[a][1] = A[a][1] + s0 * E01[a] + s2 * E12[a] + s0 * s2 * G[a];
+            J[a][2] = A[a][2] + s0 * E02[a] + s1 * E12[a] + s0 * s1 * G[a];
+        }
+        det = det3(J[0][0], J[0][1], J[0][2], J[1][0], J[1][1], J[1][2], J[2][0], J[2][1], J[2][2]);
+        if (!(det > T(0))) {
+            xi[0] = s0;
+            xi[1] = s1;
+            xi[2] = s2;
+            return ST_FOLD;
+        }
+        const T d0 = det3(F[0], J[0][1], J[0][2], F[1], J[1][1], J[1][2], F[2], J[2][1], J[2][2]) / det;
+        const T d1 = det3(J[0][0], F[0], J[0][2], J[1][0], F[1], J[1][2], J[2][0], F[2], J[2][2]) / det;
+        const T d2 = det3(J[0][0], J[0][1], F[0], J[1][0], J[1][1], F[1], J[2][0], J[2][1], F[2]) / det;
+        s0 -= d0;
+        s1 -= d1;
+        s2 -= d2;
+        if (fmax(fmax(fabs(d0), fabs(d1)), fabs(d2)) <= tol) {
+            xi[0] = s0;
+            xi[1] = s1;
+            xi[2] = s2;
+            return ST_OK;
+        }
+    }
+    xi[0] = s0;
+    xi[1] = s1;
+    xi[2] = s2;
+    return ST_NEWTON;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ int newton_solve(const T P[8][3], int max_iter, T tol, T xi[3], int *iters)
+{
+    if (DIM == 2) return newton_solve2<T>(P, max_iter, tol, xi, iters);
+    return newton_solve3<T>(P, max_iter, tol, xi, iters);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Appendix: cardinal Z-spline basis functions (piecewise form, any argument)
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T zspline(int m, T x)
+{
+    const T ax = fabs(x), x2 = ax * ax, x3 = x2 * ax;
+    if (m == 0) return ax < T(1) ? T(1) - ax : T(0);
+    if (m == 1) {
+        if (ax <= T(1)) return T(1) - T(2.5) * x2 + T(1.5) * x3;
+        if (ax <= T(2)) return T(0.5) * (T(2) - ax) * (T(2) - ax) * (T(1) - ax);
+        return T(0);
+    }
+    const T x4 = x3 * ax, x5 = x4 * ax;
+    if (ax <= T(1))
+        return T(1) - T(15.0 / 12.0) * x2 - T(35.0 / 12.0) * x3 + T(63.0 / 12.0) * x4 - T(25.0 / 12.0) * x5;
+    if (ax <= T(2))
+        return T(-4) + T(75.0 / 4.0) * ax - T(245.0 / 8.0) * x2 + T(545.0 / 24.0) * x3 - T(63.0 / 8.0) * x4
+               + T(25.0 / 24.0) * x5;
+    if (ax <= T(3))
+        return T(18) - T(153.0 / 4.0) * ax + T(255.0 / 8.0) * x2 - T(313.0 / 24.0) * x3 + T(21.0 / 8.0) * x4
+               - T(5.0 / 24.0) * x5;
+    return T(0);
+}
+
+// Weights of the 2m+2 taps c-m .. c+m+1 at local coordinate xi (argument of tap k: m - k + xi).
+template <typename T>
+__device__ __forceinline__ void zs_weights(int m, T xi, T w[6])
+{
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = (k < 2 * m + 2) ? zspline<T>(m, T(m - k) + xi) : T(0);
+}
+
+// Sec. 2.3 jump test of one node along one axis.
+template <typename T>
+__device__ __forceinline__ bool jump_test(T hm, T h0, T hp, T thr)
+{
+    const T dp = hp - h0, dm = h0 - hm;
+    return fabs(dp - dm) > thr * fmax(fabs(dp), fabs(dm));
+}
+
+// ------------------------------------------------------------------------------------------------
+// counters: warp + block aggregation, one global atomic per counter and block
+// ------------------------------------------------------------------------------------------------
+struct LocalCounters {
+    unsigned int targets, fl, fn, ff, hops, hops_max, iters, iters_max, f64, oh0, oh1, oh2, fallback;
+    __device__ __forceinline__ void clear()
+    {
+        targets = fl = fn = ff = hops = hops_max = iters = iters_max = f64 = oh0 = oh1 = oh2 = fallback = 0u;
+    }
+};
+
+__device__ __forceinline__ unsigned int warp_sum(unsigned int v) { return __reduce_add_sync(0xffffffffu, v); }
+__device__ __forceinline__ unsigned int warp_max(unsigned int v) { return __reduce_max_sync(0xffffffffu, v); }
+
+// Must be called by every thread of the block (after its work loop).
+__device__ __forceinline__ void flush_counters(const LocalCounters &c, DevCounters *g)
+{
+    if (g == nullptr) return;
+    __shared__ unsigned long long s[13];
+    if (threadIdx.x < 13) s[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned int v[13] = {warp_sum(c.targets), warp_sum(c.fl),   warp_sum(c.fn),    warp_sum(c.ff),
+                          warp_sum(c.hops),    warp_max(c.hops_max), warp_sum(c.iters), warp_max(c.iters_max),
+                          warp_sum(c.f64),     warp_sum(c.oh0),  warp_sum(c.oh1),   warp_sum(c.oh2),
+                          warp_sum(c.fallback)};
+    if ((threadIdx.x & 31) == 0) {
+        for (int q = 0; q < 13; ++q) {
+            if (q == 5 || q == 7)
+                atomicMax(&s[q], (unsigned long long)v[q]);
+            else if (v[q])
+                atomicAdd(&s[q], (unsigned long long)v[q]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *dst[13] = {&g->targets,   &g->fail_locate,   &g->fail_newton,   &g->fail_fold,
+                                       &g->hops_sum,  &g->hops_max,      &g->iters_sum,     &g->iters_max,
+                                       &g->newton_f64, &g->order_hist[0], &g->order_hist[1], &g->order_hist[2],
+                                       &g->tiles_fallback};
+        for (int q = 0; q < 13; ++q) {
+            if (q == 5 || q == 7) {
+                if (s[q]) atomicMax(dst[q], s[q]);
+            } else if (s[q]) {
+                atomicAdd(dst[q], s[q]);
+            }
+        }
+    }
+}

@@ -1,0 +1,54 @@
+// sl_internal.h -- host-side grid object and kernel launchers of libsl.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sl_device.cuh"
+
+struct sl_grid {
+    sl_grid_desc desc;          // copy of the descriptor (velocity_params points at vel_params)
+    double vel_params[SL_MAX_VEL_PARAMS];
+    int dim, nfields, dtype, ds; // ds: values per node in a displacement buffer (2 in 2-D, 4 in 3-D)
+    int64_t n[3], N;
+    double dx[3];
+    size_t tsize;                // bytes per scalar
+    // carved from the caller's workspace
+    char *ws;
+    size_t ws_bytes;
+    DevCounters *counters;
+    double *partials;            // moments: SL_MOMENT_BLOCKS x 8
+    double *moment_out;          // 8 doubles
+    uint8_t *flags;              // N
+    void *D[2];                  // two displacement buffers (ping-pong for the pipelined step)
+    int dcur;                    // index of the current displacement
+    int device, num_sms;
+    unsigned long long launches;  // kernels launched by this grid's calls (host-side count)
+};
+
+#define SL_MOMENT_BLOCKS 512
+
+// precision-dispatched launchers (sl_kernels.cu)
+template <typename T>
+struct Launch {
+    static cudaError_t advect(const sl_grid *g, void *D, double t, double dt, cudaStream_t s);
+    static cudaError_t flags(const sl_grid *g, const void *const *in, uint8_t *flags, cudaStream_t s);
+    static cudaError_t remap_generic(const sl_grid *g, const void *D, const uint8_t *flags, const void *const *in,
+                                     void *const *out, const sl_remap_debug *dbg, cudaStream_t s);
+    static cudaError_t moments(const sl_grid *g, const void *field, int pmax, cudaStream_t s);
+    static cudaError_t copy_disp(const sl_grid *g, const void *src, int64_t src_stride, void *dst,
+                                 int64_t dst_stride, cudaStream_t s);
+    // tiled / fused kernels (sl_tiled.cu)
+    static bool tiled_supported(const sl_grid *g);
+    static cudaError_t remap_tiled(const sl_grid *g, const void *D, const void *const *in, void *const *out,
+                                   cudaStream_t s);
+    static cudaError_t step_fused(const sl_grid *g, const void *D, void *D_next, double t_next, double dt,
+                                  const void *const *in, void *const *out, cudaStream_t s);
+};
+
+// shared argument builders (sl_kernels.cu)
+template <typename T>
+GridArgs<T> make_grid_args(const sl_grid *g);
+template <typename T>
+VelArgs<T> make_vel_args(const sl_grid *g, double t, double dt);
+int grid_stride_blocks(const sl_grid *g, long long work, int threads);

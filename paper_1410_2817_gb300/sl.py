@@ -1,0 +1,330 @@
+"""Python binding of libsl.so (include/sl.h): argument marshalling only.
+
+The functions carry the C names.  Device buffers are torch CUDA tensors (only their data pointers
+cross the boundary); streams default to torch's current CUDA stream.  Every step of the method runs
+in the library's CUDA kernels: there is no Python or CPU fallback, and a missing library raises.
+
+``Grid`` wraps a grid handle with its workspace tensor for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsl.so")
+
+SL_OK, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_NOMEM, SL_ERR_BUDGET = 0, 1, 2, 3, 4
+SL_ERR_LOCATE, SL_ERR_NEWTON, SL_ERR_FOLD, SL_ERR_UNSUPPORTED = 5, 6, 7, 8
+SL_F64, SL_F32 = 0, 1
+SL_RK4 = 0
+VELOCITY = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5}
+SL_NEWTON_F64, SL_NEWTON_MIXED = 0, 1
+SL_FAIL_KEEP, SL_FAIL_ERROR = 0, 1
+SL_START_BACKWARD, SL_START_PAPER = 0, 1
+SL_KERNEL_AUTO, SL_KERNEL_GENERIC, SL_KERNEL_TILED = 0, 1, 2
+
+_DTYPES = {SL_F64: torch.float64, SL_F32: torch.float32}
+
+
+class SLError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class sl_grid_desc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("n", C.c_int64 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("nfields", C.c_int), ("dtype", C.c_int), ("max_order", C.c_int), ("limiter_threshold", C.c_double),
+        ("integrator", C.c_int), ("velocity_kind", C.c_int), ("velocity_params", C.POINTER(C.c_double)),
+        ("n_velocity_params", C.c_int), ("newton_mode", C.c_int), ("newton_max_iter", C.c_int),
+        ("walk_max", C.c_int), ("fail_policy", C.c_int), ("walk_start", C.c_int), ("kernel", C.c_int),
+    ]
+
+
+class sl_diag(C.Structure):
+    _fields_ = [(name, C.c_uint64) for name in (
+        "targets", "fail_locate", "fail_newton", "fail_fold", "hops_sum", "hops_max", "iters_sum", "iters_max",
+        "newton_f64")] + [("order_hist", C.c_uint64 * 3), ("tiles_fallback", C.c_uint64),
+                    ("kernel_launches", C.c_uint64)]
+
+    def as_dict(self):
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "order_hist"}
+        d["order_hist"] = [int(v) for v in self.order_hist]
+        return d
+
+
+class sl_remap_debug(C.Structure):
+    _fields_ = [("cell", C.c_void_p), ("xi", C.c_void_p), ("order", C.c_void_p), ("status", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libsl.so (built in-tree by paper_1410_2817_gb300.build).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1410_2817_gb300.build.build() "
+                               "(the CUDA path has no fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+        pp = C.POINTER(C.c_void_p)
+        sig = {
+            "sl_grid_workspace_bytes": (C.c_size_t, [C.POINTER(sl_grid_desc)]),
+            "sl_create_grid": (C.c_int, [C.POINTER(sl_grid_desc), vp, C.c_size_t, C.POINTER(vp)]),
+            "sl_destroy_grid": (C.c_int, [vp]),
+            "sl_advect_nodes": (C.c_int, [vp, C.c_double, C.c_double, vp]),
+            "sl_remap_fields": (C.c_int, [vp, pp, pp, vp]),
+            "sl_remap_fields_debug": (C.c_int, [vp, pp, pp, C.POINTER(sl_remap_debug), vp]),
+            "sl_step": (C.c_int, [vp, pp, pp, C.c_double, C.c_double, C.c_int, vp]),
+            "sl_moments": (C.c_int, [vp, vp, C.c_int, dp, vp]),
+            "sl_compute_flags": (C.c_int, [vp, pp, vp, vp]),
+            "sl_set_displacement": (C.c_int, [vp, vp, i64, vp]),
+            "sl_get_displacement": (C.c_int, [vp, vp, i64, vp]),
+            "sl_get_diagnostics": (C.c_int, [vp, C.POINTER(sl_diag), vp]),
+            "sl_reset_diagnostics": (C.c_int, [vp, vp]),
+            "sl_status_string": (C.c_char_p, [C.c_int]),
+            "sl_last_error": (C.c_char_p, []),
+            "sl_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str):
+    if status != SL_OK:
+        L = lib()
+        detail = L.sl_status_string(status).decode()
+        extra = L.sl_last_error().decode()
+        raise SLError(status, where, f"{detail}; {extra}" if extra else detail)
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _planes(ts: Sequence[torch.Tensor]):
+    arr = (C.c_void_p * len(ts))()
+    for q, t in enumerate(ts):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("field planes must be contiguous CUDA tensors")
+        arr[q] = t.data_ptr()
+    return C.cast(arr, C.POINTER(C.c_void_p)), arr
+
+
+# ------------------------------------------------------------------------------------------------
+# thin wrappers with the C names
+# ------------------------------------------------------------------------------------------------
+def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), max_order=1,
+              limiter_threshold=0.25, velocity="uniform", velocity_params=(0.0, 0.0, 0.0),
+              newton_mode=None, newton_max_iter=0, walk_max=0, fail_policy=SL_FAIL_KEEP,
+              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO):
+    d = sl_grid_desc()
+    d.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    d.n[:] = [int(v) for v in nn]
+    d.lo[:] = [float(v) for v in list(lo) + [0.0] * (3 - len(lo))]
+    d.hi[:] = [float(v) for v in list(hi) + [1.0] * (3 - len(hi))]
+    d.nfields, d.dtype, d.max_order = nfields, dtype, max_order
+    d.limiter_threshold = float(limiter_threshold)
+    d.integrator = SL_RK4
+    d.velocity_kind = VELOCITY[velocity] if isinstance(velocity, str) else int(velocity)
+    params = (C.c_double * max(1, len(velocity_params)))(*[float(v) for v in velocity_params])
+    d.velocity_params = C.cast(params, C.POINTER(C.c_double))
+    d.n_velocity_params = len(velocity_params)
+    d._params_keepalive = params
+    if newton_mode is None:
+        newton_mode = SL_NEWTON_MIXED if dtype == SL_F32 else SL_NEWTON_F64
+    d.newton_mode, d.newton_max_iter, d.walk_max = newton_mode, newton_max_iter, walk_max
+    d.fail_policy, d.walk_start, d.kernel = fail_policy, walk_start, kernel
+    return d
+
+
+def sl_grid_workspace_bytes(desc: sl_grid_desc) -> int:
+    return int(lib().sl_grid_workspace_bytes(C.byref(desc)))
+
+
+def sl_create_grid(desc: sl_grid_desc, workspace: torch.Tensor) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().sl_create_grid(C.byref(desc), C.c_void_p(workspace.data_ptr()),
+                                workspace.numel() * workspace.element_size(), C.byref(h)), "sl_create_grid")
+    return h
+
+
+def sl_destroy_grid(h):
+    _check(lib().sl_destroy_grid(h), "sl_destroy_grid")
+
+
+def sl_advect_nodes(h, t: float, dt: float, stream=None):
+    _check(lib().sl_advect_nodes(h, float(t), float(dt), _stream(stream)), "sl_advect_nodes")
+
+
+def sl_remap_fields(h, fin: Sequence[torch.Tensor], fout: Sequence[torch.Tensor], stream=None):
+    pi, _a = _planes(fin)
+    po, _b = _planes(fout)
+    _check(lib().sl_remap_fields(h, pi, po, _stream(stream)), "sl_remap_fields")
+
+
+def sl_remap_fields_debug(h, fin, fout, cell=None, xi=None, order=None, status=None, stream=None):
+    pi, _a = _planes(fin)
+    po, _b = _planes(fout)
+    dbg = sl_remap_debug()
+    for name, t in (("cell", cell), ("xi", xi), ("order", order), ("status", status)):
+        setattr(dbg, name, t.data_ptr() if t is not None else None)
+    _check(lib().sl_remap_fields_debug(h, pi, po, C.byref(dbg), _stream(stream)), "sl_remap_fields_debug")
+
+
+def sl_step(h, fields, scratch, t0: float, dt: float, nsteps: int, stream=None):
+    pf, _a = _planes(fields)
+    ps, _b = _planes(scratch)
+    _check(lib().sl_step(h, pf, ps, float(t0), float(dt), int(nsteps), _stream(stream)), "sl_step")
+
+
+def sl_moments(h, field: torch.Tensor, pmax: int = 4, stream=None):
+    out = (C.c_double * (pmax + 1))()
+    _check(lib().sl_moments(h, C.c_void_p(field.data_ptr()), int(pmax), out, _stream(stream)), "sl_moments")
+    return [float(v) for v in out]
+
+
+def sl_compute_flags(h, fields, flags_out: torch.Tensor, stream=None):
+    pf, _a = _planes(fields)
+    _check(lib().sl_compute_flags(h, pf, C.c_void_p(flags_out.data_ptr()), _stream(stream)), "sl_compute_flags")
+
+
+def sl_set_displacement(h, D: torch.Tensor, stride: int, stream=None):
+    _check(lib().sl_set_displacement(h, C.c_void_p(D.data_ptr()), int(stride), _stream(stream)),
+           "sl_set_displacement")
+
+
+def sl_get_displacement(h, D_out: torch.Tensor, stride: int, stream=None):
+    _check(lib().sl_get_displacement(h, C.c_void_p(D_out.data_ptr()), int(stride), _stream(stream)),
+           "sl_get_displacement")
+
+
+def sl_get_diagnostics(h, stream=None) -> dict:
+    d = sl_diag()
+    _check(lib().sl_get_diagnostics(h, C.byref(d), _stream(stream)), "sl_get_diagnostics")
+    return d.as_dict()
+
+
+def sl_reset_diagnostics(h, stream=None):
+    _check(lib().sl_reset_diagnostics(h, _stream(stream)), "sl_reset_diagnostics")
+
+
+def sl_status_string(status: int) -> str:
+    return lib().sl_status_string(int(status)).decode()
+
+
+def sl_version() -> str:
+    return lib().sl_version().decode()
+
+
+# ------------------------------------------------------------------------------------------------
+# convenience object
+# ------------------------------------------------------------------------------------------------
+class Grid:
+    """A grid handle plus the workspace tensor it borrows (allocated through torch)."""
+
+    def __init__(self, dim, n, nfields, dtype=SL_F32, device="cuda", **kw):
+        self.desc = make_desc(dim, n, nfields, dtype, **kw)
+        self.dim, self.nfields, self.dtype = dim, nfields, dtype
+        self.n = tuple(int(v) for v in n)
+        self.torch_dtype = _DTYPES[dtype]
+        nbytes = sl_grid_workspace_bytes(self.desc)
+        if nbytes == 0:
+            raise SLError(SL_ERR_ARG, "Grid", "invalid grid descriptor")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.handle = sl_create_grid(self.desc, self.workspace)
+
+    @property
+    def shape(self):
+        return tuple(reversed(self.n[: self.dim]))
+
+    @property
+    def nnodes(self):
+        p = 1
+        for v in self.n[: self.dim]:
+            p *= v
+        return p
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            sl_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_fields(self):
+        return torch.empty((self.nfields,) + self.shape, dtype=self.torch_dtype, device=self.workspace.device)
+
+    def advect(self, t, dt, stream=None):
+        sl_advect_nodes(self.handle, t, dt, stream)
+
+    def remap(self, fin: torch.Tensor, fout: torch.Tensor, stream=None):
+        sl_remap_fields(self.handle, list(fin), list(fout), stream)
+
+    def remap_debug(self, fin, fout, stream=None):
+        dev = fin.device
+        N = self.nnodes
+        cell = torch.empty(self.shape, dtype=torch.int64, device=dev)
+        xi = torch.empty(self.shape + (self.dim,), dtype=torch.float64, device=dev)
+        order = torch.empty((self.nfields,) + self.shape, dtype=torch.uint8, device=dev)
+        status = torch.empty(self.shape, dtype=torch.uint8, device=dev)
+        sl_remap_fields_debug(self.handle, list(fin), list(fout), cell, xi, order, status, stream)
+        del N
+        return cell, xi, order, status
+
+    def step(self, fields: torch.Tensor, scratch: torch.Tensor, t0, dt, nsteps, stream=None):
+        sl_step(self.handle, list(fields), list(scratch), t0, dt, nsteps, stream)
+
+    def moments(self, field: torch.Tensor, pmax=4, stream=None):
+        return sl_moments(self.handle, field, pmax, stream)
+
+    def flags(self, fields: torch.Tensor, stream=None):
+        out = torch.empty(self.shape, dtype=torch.uint8, device=fields.device)
+        sl_compute_flags(self.handle, list(fields), out, stream)
+        return out
+
+    def set_displacement(self, D: torch.Tensor, stream=None):
+        D = D.contiguous()
+        sl_set_displacement(self.handle, D, D.shape[-1], stream)
+
+    def get_displacement(self, stream=None):
+        out = torch.empty(self.shape + (self.dim,), dtype=self.torch_dtype, device=self.workspace.device)
+        sl_get_displacement(self.handle, out, self.dim, stream)
+        return out
+
+    def diagnostics(self, stream=None):
+        return sl_get_diagnostics(self.handle, stream)
+
+    def reset_diagnostics(self, stream=None):
+        sl_reset_diagnostics(self.handle, stream)
+
+
+def grid_for(workload, dtype=SL_F32, **kw) -> Grid:
+    """Grid for an inputs.Workload (same velocity, order and limiter settings)."""
+    return Grid(workload.dim, list(workload.n)[: workload.dim], workload.nfields, dtype,
+                lo=workload.lo, hi=workload.hi, max_order=workload.max_order,
+                limiter_threshold=workload.threshold, velocity=workload.velocity,
+                velocity_params=list(workload.velocity_params), **kw)
