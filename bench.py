@@ -77,7 +77,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                           stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._proc = None
@@ -242,6 +242,7 @@ def main():
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
+        time.sleep(0.3)  # nvidia-smi's first sample
     g32, f32, s32, ms32, wall32, t_end, launches = run_path(sl.SL_F32, sl.SL_NEWTON_MIXED, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
     dev_ms = sum(ms32)

@@ -179,8 +179,15 @@ __device__ __forceinline__ void walk_start_cell(int mode, const int j[3], const 
 #pragma unroll
     for (int a = 0; a < 3; ++a) c[a] = 0;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
-        c[a] = mode == SL_START_PAPER ? j[a] - (Dj[a] > T(0) ? 1 : 0) : (int)floor_t<T>(T(j[a]) - Dj[a]);
+    for (int a = 0; a < DIM; ++a) {
+        if (mode == SL_START_PAPER) {
+            c[a] = j[a] - (Dj[a] > T(0) ? 1 : 0);
+        } else {
+            // clamped so that a garbage displacement cannot overflow the walk's integer steps
+            const T s = fmin(fmax(T(j[a]) - Dj[a], T(j[a]) - T(65536)), T(j[a]) + T(65536));
+            c[a] = isfinite(s) ? (int)floor_t<T>(s) : j[a];
+        }
+    }
 }
 
 // Sec. 2.2 element search from element c: invert (Newton in precision TN) and, while a local
