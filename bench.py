@@ -186,6 +186,30 @@ def run_reference(args):
     return 0
 
 
+def kernel_only(args):
+    """Launch only sl_remap_fields or sl_step (FP32 production path) on the swirl workload, for
+    profilers; prints the mean CUDA-event time per call."""
+    import torch
+    from paper_1410_2817_gb300 import build, inputs, sl
+    build.build()
+    wl = inputs.workload_swirl(args.n)
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(f)
+    g.advect(0.5, wl.dt)
+    for _ in range(args.warmup):
+        g.remap(f, out) if args.mode == "remap" else g.step(f, out, 0.5, wl.dt, 1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        g.remap(f, out) if args.mode == "remap" else g.step(f, out, 0.5, wl.dt, 1)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": args.mode, "n": args.n, "calls": args.steps, "ms_per_call": a.elapsed_time(b) / args.steps,
+                      "diagnostics": g.diagnostics()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,10 +218,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="full", choices=["full", "remap", "step"],
+                    help="remap/step: only launch that call --steps times (for profilers); prints its timing")
+    ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode != "full":
+        return kernel_only(args)
 
     import torch
     dist, rank, ws, local = _dist()

@@ -91,7 +91,7 @@ static const char *check_desc(const sl_grid_desc *d)
 }
 
 struct Layout {
-    size_t counters, partials, moment_out, flags, D0, D1, total;
+    size_t counters, partials, moment_out, flags, flags2, D0, D1, total;
 };
 
 static Layout layout_of(const sl_grid_desc *d)
@@ -109,6 +109,8 @@ static Layout layout_of(const sl_grid_desc *d)
     L.moment_out = off;
     off += align256(sizeof(double) * 8);
     L.flags = off;
+    off += align256((size_t)N);
+    L.flags2 = off;
     off += align256((size_t)N);
     L.D0 = off;
     off += align256((size_t)N * ds * ts);
@@ -161,6 +163,7 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     g->partials = (double *)(g->ws + L.partials);
     g->moment_out = (double *)(g->ws + L.moment_out);
     g->flags = (uint8_t *)(g->ws + L.flags);
+    g->flags2 = (uint8_t *)(g->ws + L.flags2);
     g->D[0] = g->ws + L.D0;
     g->D[1] = g->ws + L.D1;
     g->dcur = 0;
@@ -223,7 +226,7 @@ template <typename T>
 static cudaError_t remap_impl(sl_grid *g, const void *D, const void *const *in, void *const *out,
                               const sl_remap_debug *dbg, cudaStream_t s)
 {
-    if (!dbg && use_tiled<T>(g)) return counted(g, Launch<T>::remap_tiled(g, D, in, out, s), 1);
+    if (!dbg && use_tiled<T>(g)) return counted(g, Launch<T>::remap_tiled(g, D, in, out, s), tiled_kernels_per_call(g));
     cudaError_t e = counted(g, Launch<T>::flags(g, in, g->flags, s), 1);
     if (e != cudaSuccess) return e;
     return counted(g, Launch<T>::remap_generic(g, D, g->flags, in, out, dbg, s), 1);
@@ -287,7 +290,7 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
         if (fused) {
             const int nx = g->dcur ^ 1;
             e = counted(g, Launch<T>::step_fused(g, g->D[g->dcur], k + 1 < nsteps ? g->D[nx] : nullptr, t + dt, dt,
-                                                 cur, nxt, s), 1);
+                                                 cur, nxt, s), tiled_kernels_per_call(g));
             if (e != cudaSuccess) return e;
             if (k + 1 < nsteps) g->dcur = nx;
         } else {

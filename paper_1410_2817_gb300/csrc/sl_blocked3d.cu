@@ -1,0 +1,294 @@
+// sl_blocked3d.cu -- the FP32 production kernels of the FSL step (arXiv:1410.2817) for 3-D grids.
+//
+// A 3-D departure window with a 4x4x4 stencil halo is many times the size of its target block
+// (the 3-D workloads move nodes by ~15 cells per step), so the 3-D path does not stage windows in
+// shared memory.  Instead:
+//   * box_flags: the jump flags of Sec. 2.3 are computed once per node and OR-ed over every
+//     element's 4x4x4 stencil [c-1, c+2]^3 (separable: x, then y, then z), so choosing the order
+//     of a target (Sec. 2.3) costs one byte load;
+//   * remap_blocked3d_kernel: one thread per target; a CTA covers an 8x8x4 block of targets so
+//     that the element search (Sec. 2.2, Newton in FP32 with FP64 re-solves near faces) and the
+//     64-tap tricubic sum (eq. multiZ) of neighbouring targets hit the same L1 lines.  The fused
+//     variant also integrates the next step's trajectories (eq. vel) for its own nodes.
+#include <math.h>
+#include <string.h>
+
+#include "sl_internal.h"
+
+namespace {
+
+constexpr int BX = 8, BY = 8, BZ = 4, NT3 = BX * BY * BZ;
+constexpr float FACE_MARGIN3 = 2e-5f;
+
+struct Geo3 {
+    int n0, n1, n2;
+};
+
+__device__ __forceinline__ int wrap3(int k, int n)
+{
+    int r = k % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ long long lin3(const Geo3 &g, int x, int y, int z)
+{
+    return ((long long)wrap3(z, g.n2) * g.n1 + wrap3(y, g.n1)) * g.n0 + wrap3(x, g.n0);
+}
+
+struct Fields3 {
+    const float *in[SL_MAX_FIELDS];
+    float *out[SL_MAX_FIELDS];
+};
+
+// ---- Sec. 2.3 flags and their OR over [c-1, c+2] along one axis -----------------------------
+__global__ void __launch_bounds__(256) flags3d_kernel(Geo3 g, int nfields, float thr, Fields3 f, uint8_t *flags)
+{
+    const long long N = (long long)g.n0 * g.n1 * g.n2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.n0), y = (int)((i / g.n0) % g.n1), z = (int)(i / ((long long)g.n0 * g.n1));
+        unsigned bits = 0;
+        if (thr >= 0.f) {
+            const long long xm = lin3(g, x - 1, y, z), xp = lin3(g, x + 1, y, z);
+            const long long ym = lin3(g, x, y - 1, z), yp = lin3(g, x, y + 1, z);
+            const long long zm = lin3(g, x, y, z - 1), zp = lin3(g, x, y, z + 1);
+            for (int q = 0; q < nfields; ++q) {
+                const float *h = f.in[q];
+                const float h0 = __ldg(h + i);
+                const bool hit = jump_test<float>(__ldg(h + xm), h0, __ldg(h + xp), thr) ||
+                                 jump_test<float>(__ldg(h + ym), h0, __ldg(h + yp), thr) ||
+                                 jump_test<float>(__ldg(h + zm), h0, __ldg(h + zp), thr);
+                bits |= hit ? (1u << q) : 0u;
+            }
+        }
+        flags[i] = (uint8_t)bits;
+    }
+}
+
+// out[c] = OR of in[c-1 .. c+2] along `axis`
+__global__ void __launch_bounds__(256) box_or_kernel(Geo3 g, int axis, const uint8_t *in, uint8_t *out)
+{
+    const long long N = (long long)g.n0 * g.n1 * g.n2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.n0), y = (int)((i / g.n0) % g.n1), z = (int)(i / ((long long)g.n0 * g.n1));
+        uint8_t r = 0;
+#pragma unroll
+        for (int o = -1; o <= 2; ++o) {
+            const long long k = axis == 0 ? lin3(g, x + o, y, z) : axis == 1 ? lin3(g, x, y + o, z) : lin3(g, x, y, z + o);
+            r |= in[k];
+        }
+        out[i] = r;
+    }
+}
+
+__device__ __forceinline__ void cubic_w(float x, float w[4])
+{
+    const float y = 1.f - x, x2 = x * x, y2 = y * y;
+    w[0] = -0.5f * x * y2;
+    w[1] = fmaf(x2, fmaf(1.5f, x, -2.5f), 1.f);
+    w[2] = fmaf(y2, fmaf(1.5f, y, -2.5f), 1.f);
+    w[3] = -0.5f * x2 * y;
+}
+
+// Sec. 2.2 element search in 3-D from element c, Newton in precision TN; D padded to 4 floats.
+template <typename TN>
+__device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D, int max_iter, int walk_max,
+                                     const int j[3], int c[3], TN xi[3], int &hops, int &iters)
+{
+    const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(1e-5);
+    const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(1e-5);
+    for (int hop = 0; hop < walk_max; ++hop) {
+        TN P[8][3];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int kx = c[0] + (v & 1), ky = c[1] + ((v >> 1) & 1), kz = c[2] + (v >> 2);
+            const float4 d = __ldg(D + lin3(g, kx, ky, kz));
+            P[v][0] = TN(kx - j[0]) + TN(d.x);
+            P[v][1] = TN(ky - j[1]) + TN(d.y);
+            P[v][2] = TN(kz - j[2]) + TN(d.z);
+        }
+        int it = 0;
+        const int st = newton_solve3<TN>(P, max_iter, tol, xi, &it);
+        hops += 1;
+        iters += it;
+        bool finite = true, inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            finite &= finite_t(xi[a]);
+            inside &= xi[a] >= -slack && xi[a] <= TN(1) + slack;
+        }
+        if (!finite) return st == ST_OK ? ST_NEWTON : st;
+        if (inside) return st;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (xi[a] < -slack)
+                c[a] -= 1;
+            else if (xi[a] > TN(1) + slack)
+                c[a] += 1;
+        }
+    }
+    return ST_LOCATE;
+}
+
+struct Blocked3Args {
+    Geo3 g;
+    int nfields, max_order, max_iter, walk_max;
+    const float4 *D;
+    float4 *D_next;
+    const uint8_t *box;   // OR of the flags over each element's 4x4x4 stencil
+    Fields3 f;
+    DevCounters *counters;
+};
+
+template <bool FUSED>
+__global__ void __launch_bounds__(NT3, 2) remap_blocked3d_kernel(const Blocked3Args a, const VelArgs<float> vn)
+{
+    const Geo3 &g = a.g;
+    const int jx = blockIdx.x * BX + threadIdx.x % BX;
+    const int jy = blockIdx.y * BY + (threadIdx.x / BX) % BY;
+    const int jz = blockIdx.z * BZ + threadIdx.x / (BX * BY);
+    LocalCounters cnt;
+    cnt.clear();
+    if (jx < g.n0 && jy < g.n1 && jz < g.n2) {
+        const long long jj = ((long long)jz * g.n1 + jy) * g.n0 + jx;
+        const int j[3] = {jx, jy, jz};
+        const float4 dj = __ldg(a.D + jj);
+        const float djv[3] = {dj.x, dj.y, dj.z};
+        int c[3], c0[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float s = fminf(fmaxf((float)j[q] - djv[q], (float)j[q] - 65536.f), (float)j[q] + 65536.f);
+            c0[q] = c[q] = finite_t(s) ? (int)floorf(s) : j[q];
+        }
+        int hops = 0, iters = 0;
+        float xf[3] = {0.f, 0.f, 0.f};
+        int st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters);
+        bool redo = st != ST_OK;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) redo |= fabsf(xf[q]) < FACE_MARGIN3 || fabsf(1.f - xf[q]) < FACE_MARGIN3;
+        if (redo) {
+            double xd[3] = {0.0, 0.0, 0.0};
+            if (st == ST_LOCATE || st == ST_FOLD)
+                for (int q = 0; q < 3; ++q) c[q] = c0[q];
+            st = walk3<double>(g, a.D, a.max_iter, a.walk_max, j, c, xd, hops, iters);
+            for (int q = 0; q < 3; ++q) xf[q] = (float)xd[q];
+            cnt.f64 += 1;
+        }
+        cnt.targets = 1;
+        cnt.hops = hops;
+        cnt.hops_max = hops;
+        cnt.iters = iters;
+        cnt.iters_max = iters;
+        if (st != ST_OK) {
+            cnt.fl = st == ST_LOCATE;
+            cnt.fn = st == ST_NEWTON;
+            cnt.ff = st == ST_FOLD;
+            for (int q = 0; q < a.nfields; ++q) a.f.out[q][jj] = __ldg(a.f.in[q] + jj);
+        } else {
+            const unsigned bits = a.max_order >= 1 ? (unsigned)__ldg(a.box + lin3(g, c[0], c[1], c[2])) : 0xffu;
+            float wc[3][4];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cubic_w(xf[q], wc[q]);
+            // wrapped node offsets of the stencil c-1 .. c+2 along each axis
+            int ox[4];
+            long long oy[4], oz[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ox[k] = wrap3(c[0] - 1 + k, g.n0);
+                oy[k] = (long long)wrap3(c[1] - 1 + k, g.n1) * g.n0;
+                oz[k] = (long long)wrap3(c[2] - 1 + k, g.n2) * g.n0 * g.n1;
+            }
+            for (int q = 0; q < a.nfields; ++q) {
+                const float *h = a.f.in[q];
+                const bool lin = ((bits >> q) & 1u) != 0u;
+                cnt.oh0 += lin;
+                cnt.oh1 += !lin;
+                float sum = 0.f;
+                if (lin) {
+                    // Z~0: trilinear over the element's 8 vertices (taps 1, 2 of each axis)
+                    for (int kz = 1; kz <= 2; ++kz) {
+                        const float wz = kz == 1 ? 1.f - xf[2] : xf[2];
+                        float sy = 0.f;
+                        for (int ky = 1; ky <= 2; ++ky) {
+                            const float wy = ky == 1 ? 1.f - xf[1] : xf[1];
+                            const float *row = h + oz[kz] + oy[ky];
+                            const float r = fmaf(xf[0], __ldg(row + ox[2]), (1.f - xf[0]) * __ldg(row + ox[1]));
+                            sy = fmaf(wy, r, sy);
+                        }
+                        sum = fmaf(wz, sy, sum);
+                    }
+                } else {
+#pragma unroll
+                    for (int kz = 0; kz < 4; ++kz) {
+                        float sy = 0.f;
+#pragma unroll
+                        for (int ky = 0; ky < 4; ++ky) {
+                            const float *row = h + oz[kz] + oy[ky];
+                            const float r = fmaf(wc[0][3], __ldg(row + ox[3]),
+                                                 fmaf(wc[0][2], __ldg(row + ox[2]),
+                                                      fmaf(wc[0][1], __ldg(row + ox[1]), wc[0][0] * __ldg(row + ox[0]))));
+                            sy = fmaf(wc[1][ky], r, sy);
+                        }
+                        sum = fmaf(wc[2][kz], sy, sum);
+                    }
+                }
+                a.f.out[q][jj] = sum;
+            }
+        }
+        if (FUSED && a.D_next != nullptr) {
+            float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], vn.lo[2] + (float)jz * vn.dx[2]};
+            float d[3];
+            rk4_cells<float, 3>(vn, X, d);
+            a.D_next[jj] = make_float4(d[0], d[1], d[2], 0.f);
+        }
+    }
+    flush_counters(cnt, a.counters);
+}
+
+}  // namespace
+
+// box flags of a 3-D FP32 grid into g->flags (uses D[other] as scratch? no: two byte buffers are
+// carved from the flags region and the spare displacement buffer is never touched)
+cudaError_t launch_box_flags3d(const sl_grid *g, const void *const *in, uint8_t *flags, uint8_t *tmp, cudaStream_t s)
+{
+    Geo3 geo = {(int)g->n[0], (int)g->n[1], (int)g->n[2]};
+    Fields3 f;
+    memset(&f, 0, sizeof(f));
+    for (int q = 0; q < g->nfields; ++q) f.in[q] = (const float *)in[q];
+    const int blocks = grid_stride_blocks(g, g->N, 256);
+    flags3d_kernel<<<blocks, 256, 0, s>>>(geo, g->nfields, (float)g->desc.limiter_threshold, f, flags);
+    box_or_kernel<<<blocks, 256, 0, s>>>(geo, 0, flags, tmp);
+    box_or_kernel<<<blocks, 256, 0, s>>>(geo, 1, tmp, flags);
+    box_or_kernel<<<blocks, 256, 0, s>>>(geo, 2, flags, tmp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, const uint8_t *box, double t_next,
+                             double dt, bool fused, const void *const *in, void *const *out, cudaStream_t s)
+{
+    Blocked3Args a;
+    memset(&a, 0, sizeof(a));
+    a.g = {(int)g->n[0], (int)g->n[1], (int)g->n[2]};
+    a.nfields = g->nfields;
+    a.max_order = g->desc.max_order;
+    a.max_iter = g->desc.newton_max_iter;
+    a.walk_max = g->desc.walk_max;
+    a.D = (const float4 *)D;
+    a.D_next = (float4 *)D_next;
+    a.box = box;
+    for (int q = 0; q < g->nfields; ++q) {
+        a.f.in[q] = (const float *)in[q];
+        a.f.out[q] = (float *)out[q];
+    }
+    a.counters = g->counters;
+    dim3 grid((unsigned)((g->n[0] + BX - 1) / BX), (unsigned)((g->n[1] + BY - 1) / BY),
+              (unsigned)((g->n[2] + BZ - 1) / BZ));
+    if (fused) {
+        const VelArgs<float> vn = make_vel_args<float>(g, t_next, dt);
+        remap_blocked3d_kernel<true><<<grid, NT3, 0, s>>>(a, vn);
+    } else {
+        VelArgs<float> vn;
+        memset(&vn, 0, sizeof(vn));
+        remap_blocked3d_kernel<false><<<grid, NT3, 0, s>>>(a, vn);
+    }
+    return cudaGetLastError();
+}

@@ -61,6 +61,18 @@ __device__ __forceinline__ int wrap_idx(int k, int n)
     return r < 0 ? r + n : r;
 }
 
+// Type-exact math: a float argument must never reach a double overload (GB300 runs FP64 at a
+// small fraction of its FP32 rate, so one stray conversion per tap or iteration dominates).
+__device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_t(double x) { return fabs(x); }
+__device__ __forceinline__ float max_t(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_t(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float min_t(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_t(double a, double b) { return fmin(a, b); }
+// finite: false for NaN and +-Inf, without the generic isfinite()
+__device__ __forceinline__ bool finite_t(float x) { return fabsf(x) <= 3.40282346638528859812e+38f; }
+__device__ __forceinline__ bool finite_t(double x) { return fabs(x) <= 1.79769313486231570815e+308; }
+
 __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
 
@@ -200,7 +212,7 @@ __device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T to
         const T d1 = (j11 * fy - j21 * fx) / det;
         s -= d0;
         t -= d1;
-        if (fmax(fabs(d0), fabs(d1)) <= tol) {
+        if (max_t(abs_t(d0), abs_t(d1)) <= tol) {
             xi[0] = s;
             xi[1] = t;
             return ST_OK;
@@ -266,7 +278,7 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
         s0 -= d0;
         s1 -= d1;
         s2 -= d2;
-        if (fmax(fmax(fabs(d0), fabs(d1)), fabs(d2)) <= tol) {
+        if (max_t(max_t(abs_t(d0), abs_t(d1)), abs_t(d2)) <= tol) {
             xi[0] = s0;
             xi[1] = s1;
             xi[2] = s2;
@@ -292,7 +304,7 @@ __device__ __forceinline__ int newton_solve(const T P[8][3], int max_iter, T tol
 template <typename T>
 __device__ __forceinline__ T zspline(int m, T x)
 {
-    const T ax = fabs(x), x2 = ax * ax, x3 = x2 * ax;
+    const T ax = abs_t(x), x2 = ax * ax, x3 = x2 * ax;
     if (m == 0) return ax < T(1) ? T(1) - ax : T(0);
     if (m == 1) {
         if (ax <= T(1)) return T(1) - T(2.5) * x2 + T(1.5) * x3;
@@ -324,7 +336,7 @@ template <typename T>
 __device__ __forceinline__ bool jump_test(T hm, T h0, T hp, T thr)
 {
     const T dp = hp - h0, dm = h0 - hm;
-    return fabs(dp - dm) > thr * fmax(fabs(dp), fabs(dm));
+    return abs_t(dp - dm) > thr * max_t(abs_t(dp), abs_t(dm));
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -20,6 +20,7 @@ struct sl_grid {
     double *partials;            // moments: SL_MOMENT_BLOCKS x 8
     double *moment_out;          // 8 doubles
     uint8_t *flags;              // N
+    uint8_t *flags2;             // N (second byte buffer: separable OR of flags over stencils)
     void *D[2];                  // two displacement buffers (ping-pong for the pipelined step)
     int dcur;                    // index of the current displacement
     int device, num_sms;
@@ -45,6 +46,13 @@ struct Launch {
     static cudaError_t step_fused(const sl_grid *g, const void *D, void *D_next, double t_next, double dt,
                                   const void *const *in, void *const *out, cudaStream_t s);
 };
+
+// 3-D FP32 kernels (sl_blocked3d.cu): box flags end up in `tmp`
+cudaError_t launch_box_flags3d(const sl_grid *g, const void *const *in, uint8_t *flags, uint8_t *tmp, cudaStream_t s);
+cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, const uint8_t *box, double t_next,
+                             double dt, bool fused, const void *const *in, void *const *out, cudaStream_t s);
+// kernels one tiled remap / fused step call launches
+int tiled_kernels_per_call(const sl_grid *g);
 
 // shared argument builders (sl_kernels.cu)
 template <typename T>

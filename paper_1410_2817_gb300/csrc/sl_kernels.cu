@@ -184,8 +184,8 @@ __device__ __forceinline__ void walk_start_cell(int mode, const int j[3], const 
             c[a] = j[a] - (Dj[a] > T(0) ? 1 : 0);
         } else {
             // clamped so that a garbage displacement cannot overflow the walk's integer steps
-            const T s = fmin(fmax(T(j[a]) - Dj[a], T(j[a]) - T(65536)), T(j[a]) + T(65536));
-            c[a] = isfinite(s) ? (int)floor_t<T>(s) : j[a];
+            const T s = min_t(max_t(T(j[a]) - Dj[a], T(j[a]) - T(65536)), T(j[a]) + T(65536));
+            c[a] = finite_t(s) ? (int)floor_t<T>(s) : j[a];
         }
     }
 }
@@ -215,7 +215,7 @@ __device__ __forceinline__ int walk_global(const WalkParams<TN> &w, const int n[
         bool finite = true, inside = true;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            if (!isfinite(xi[a])) finite = false;
+            if (!finite_t(xi[a])) finite = false;
             if (!(xi[a] >= -w.slack && xi[a] <= TN(1) + w.slack)) inside = false;
         }
         if (!finite) return st == ST_OK ? ST_NEWTON : st;

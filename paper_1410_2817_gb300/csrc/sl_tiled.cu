@@ -10,8 +10,8 @@
 // leaves the window, or a tile whose window does not fit, falls back to global gathers (counted).
 //
 // Precision: FP32 data and FP32 Newton; targets whose FP32 inversion failed or that lie within
-// SL_TILED_FACE_MARGIN of an element face are re-solved in FP64 (the element choice there is
-// sensitive to rounding).
+// FACE_MARGIN of an element face are re-solved in FP64 (the element choice there is sensitive to
+// rounding).
 //
 // The fused variant also integrates the next step's trajectories (eq. vel) for the tile's own
 // nodes: the velocity is given, so D(t + dt) does not depend on the fields being remapped.
@@ -55,7 +55,7 @@ __device__ __forceinline__ int wrapi(int k, int n)
 __device__ __forceinline__ int start_cell(int j, float d)
 {
     const float s = fminf(fmaxf((float)j - d, (float)j - 65536.f), (float)j + 65536.f);
-    return isfinite(s) ? (int)floorf(s) : j;
+    return finite_t(s) ? (int)floorf(s) : j;
 }
 
 __device__ __forceinline__ long long gidx(int x, int y, int n0, int n1)
@@ -100,7 +100,7 @@ __device__ __forceinline__ int walk2(const TileArgs &a, const Win &w, const floa
         const int st = newton_solve2<TN>(P, a.max_iter, tol, xi, &it);
         hops += 1;
         iters += it;
-        const bool finite = isfinite(xi[0]) && isfinite(xi[1]);
+        const bool finite = finite_t(xi[0]) && finite_t(xi[1]);
         if (!finite) return st == ST_OK ? ST_NEWTON : st;
         const bool inside = xi[0] >= -slack && xi[0] <= TN(1) + slack && xi[1] >= -slack && xi[1] <= TN(1) + slack;
         if (inside) return st;
@@ -386,11 +386,15 @@ cudaError_t launch_tiled(const sl_grid *g, const TileArgs &a, const VelArgs<floa
 
 }  // namespace
 
+// 2-D: one tiled launch; 3-D: flags + three box-OR passes + one blocked launch
+int tiled_kernels_per_call(const sl_grid *g) { return g->dim == 2 ? 1 : 5; }
+
 template <typename T>
 bool Launch<T>::tiled_supported(const sl_grid *g)
 {
-    return sizeof(T) == 4 && g->dim == 2 && g->desc.max_order <= 1 && g->desc.walk_start == SL_START_BACKWARD &&
-           g->n[0] <= (1 << 24) && tiled_smem_bytes(g->nfields) <= 200 * 1024;
+    if (sizeof(T) != 4 || g->desc.max_order > 1 || g->desc.walk_start != SL_START_BACKWARD) return false;
+    if (g->dim == 3) return true;
+    return tiled_smem_bytes(g->nfields) <= 200 * 1024;
 }
 
 template <typename T>
@@ -398,6 +402,11 @@ cudaError_t Launch<T>::remap_tiled(const sl_grid *g, const void *D, const void *
                                    cudaStream_t s)
 {
     if (!tiled_supported(g)) return cudaErrorNotSupported;
+    if (g->dim == 3) {
+        cudaError_t e = launch_box_flags3d(g, in, g->flags, g->flags2, s);
+        if (e != cudaSuccess) return e;
+        return launch_blocked3d(g, D, nullptr, g->flags2, 0.0, 0.0, false, in, out, s);
+    }
     const TileArgs a = make_tile_args(g, D, nullptr, in, out);
     VelArgs<float> vn;
     memset(&vn, 0, sizeof(vn));
@@ -409,6 +418,11 @@ cudaError_t Launch<T>::step_fused(const sl_grid *g, const void *D, void *D_next,
                                   const void *const *in, void *const *out, cudaStream_t s)
 {
     if (!tiled_supported(g)) return cudaErrorNotSupported;
+    if (g->dim == 3) {
+        cudaError_t e = launch_box_flags3d(g, in, g->flags, g->flags2, s);
+        if (e != cudaSuccess) return e;
+        return launch_blocked3d(g, D, D_next, g->flags2, t_next, dt, true, in, out, s);
+    }
     const TileArgs a = make_tile_args(g, D, D_next, in, out);
     const VelArgs<float> vn = make_vel_args<float>(g, t_next, dt);
     return launch_tiled<true>(g, a, vn, s);

@@ -456,18 +456,74 @@ def test_tiled_matches_generic_f32(sl, orc, case):
 
 
 def test_fused_step_matches_split_steps_f32(sl):
-    """sl_step on the tiled path (trajectories of step k+1 integrated inside the remap of step k)
-    equals the plain FP32 path stepping flags -> advect -> remap, up to FP32 rounding."""
+    """sl_step on the tiled path integrates the trajectories of step k+1 inside the remap of step
+    k.  Step by step (same inputs) it matches the plain FP32 path (flags -> advect -> remap) up to
+    FP32 rounding, and the displacement it leaves equals sl_advect_nodes'."""
     wl = inputs.workload_swirl(192, steps=6)
-    res = {}
-    for kname, kern in (("generic", sl.SL_KERNEL_GENERIC), ("tiled", sl.SL_KERNEL_AUTO)):
-        g = sl.grid_for(wl, sl.SL_F32, kernel=kern)
-        f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
-        s = torch.empty_like(f)
-        g.step(f, s, 0.25, wl.dt, 6)
+    gt = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_AUTO)
+    gg = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_GENERIC)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
+    t = 0.25
+    worst = 0.0
+    for k in range(4):
+        ft, fg = f.clone(), f.clone()
+        st_, sg_ = torch.empty_like(f), torch.empty_like(f)
+        gt.step(ft, st_, t, wl.dt, 1)
+        gg.step(fg, sg_, t, wl.dt, 1)
         torch.cuda.synchronize()
-        res[kname] = f.double().cpu().numpy()
-        res[kname + "_launches"] = g.diagnostics()["kernel_launches"]
-    assert np.max(np.abs(res["tiled"] - res["generic"])) <= 1e-5
-    assert res["tiled_launches"] == 1 + 6  # one advect, then one fused launch per step
-    assert res["generic_launches"] == 3 * 6
+        worst = max(worst, float((ft - fg).abs().max()))
+        f = fg
+        t += wl.dt
+    assert worst <= 2e-6, worst
+    # two fused steps: the second remap used the D the first launch integrated for t0 + dt
+    ft = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
+    gt.step(ft, torch.empty_like(ft), 0.25, wl.dt, 2)
+    d_fused = gt.get_displacement()
+    gg.advect(0.25 + wl.dt, wl.dt)
+    d_plain = gg.get_displacement()
+    assert float((d_fused - d_plain).abs().max()) <= 1e-6 * float(d_plain.abs().max())
+    l0 = gt.diagnostics()["kernel_launches"]
+    gt.step(ft, torch.empty_like(ft), 0.0, wl.dt, 6)
+    assert gt.diagnostics()["kernel_launches"] - l0 == 1 + 6  # one advect, then one launch per step
+
+
+@pytest.mark.parametrize("case", ["deform3d_32", "ragged3d", "limiter_off3d"])
+def test_blocked3d_matches_generic_f32(sl, orc, case):
+    rng = np.random.default_rng(31)
+    thr = 0.25
+    if case == "deform3d_32":
+        n = (32, 32, 32)
+        og = _og(orc, 3, n, 2, velocity="deform3d", params=[3.0])
+        D, h = orc.advect(og, 0.4, 0.03), inputs.deform3d_fields(32)
+    elif case == "ragged3d":
+        n = (19, 13, 11)
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=8, shift=(1.6, -2.2, 0.7))
+        h = np.stack([rng.standard_normal((11, 13, 19)).cumsum(axis=2) * 0.1, (rng.uniform(size=(11, 13, 19)) > 0.5) * 1.0])
+    else:
+        n, thr = (16, 16, 16), -1.0
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=9, shift=(-0.6, 3.1, 0.2))
+        h = rng.standard_normal((3, 16, 16, 16))
+    nf = h.shape[0]
+    outs, diags = {}, {}
+    for kname, kern in (("generic", sl.SL_KERNEL_GENERIC), ("tiled", sl.SL_KERNEL_TILED)):
+        g = _gpu_grid(sl, 3, n, nf, sl.SL_F32, threshold=thr, start="backward", kernel=kern)
+        hin = torch.tensor(h, dtype=torch.float32, device=DEV)
+        hout = torch.empty_like(hin)
+        g.set_displacement(torch.tensor(D, dtype=torch.float32, device=DEV))
+        g.remap(hin, hout)
+        torch.cuda.synchronize()
+        outs[kname] = hout.double().cpu().numpy()
+        diags[kname] = g.diagnostics()
+    diff = np.abs(outs["tiled"] - outs["generic"])
+    assert float(diff.max()) <= 4e-6 * max(1.0, float(np.abs(h).max())), float(diff.max())
+    assert diags["tiled"]["order_hist"] == diags["generic"]["order_hist"]
+    assert diags["tiled"]["targets"] == int(np.prod(n))
+
+
+def test_fp32_3d_step_accuracy(sl, orc):
+    wl = inputs.workload_deform3d(32, steps=4)
+    ref, got, g = _step_compare(sl, orc, wl, 4, sl.SL_F32, None)
+    l1 = np.abs(got[0] - ref[0]).sum() / np.abs(ref[0]).sum()
+    assert l1 <= 1e-5, l1
+    d = g.diagnostics()
+    assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
