@@ -150,6 +150,25 @@ sl_status sl_step(sl_grid *grid, void *const *fields, void *const *scratch, doub
  * FP64 in a fixed order.  Writes pmax+1 doubles to host_out (synchronises). */
 sl_status sl_moments(sl_grid *grid, const void *field, int pmax, double *host_out, void *stream);
 
+/* Discrete moments (as sl_moments) of one field plane, for callers that cannot allocate device
+ * memory: a host program whose allocator owns all device memory and forbids other allocations,
+ * code on a real-time path where cudaMalloc/cudaFree would synchronise the device, or a caller
+ * that only holds the field plane it was handed.  It needs no grid and no workspace and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).  The paper has no
+ * counterpart: this is a calling convenience.
+ *   dim, n, lo, hi, dtype: the grid of `field` (as in sl_grid_desc); field: device plane.
+ *   pmax: 0..7; host_out: pmax+1 doubles.  Synchronises `stream`.
+ * Its scratch is a fixed file-scope device array of 512 x 8 + 8 doubles (about 33 KB) that every
+ * GPU loading the library holds until the process exits.  pmax above 7 (the moments a scratch
+ * row holds) or more than 2^31 - 1 nodes returns SL_ERR_ARG.  Every call on a device shares the
+ * array and leaves its contents behind; each call overwrites everything it reads, so nothing
+ * needs clearing, but calls whose kernels overlap on the GPU (different streams, no ordering)
+ * race on it and must be serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current) and caches it; make
+ * that first call before any stream capture. */
+sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], const double hi[3], int dtype,
+                             const void *field, int pmax, double *host_out, void *stream);
+
 /* Jump flags of Sec. 2.3 for `fields` into flags_out (device, N bytes; bit f for field f). */
 sl_status sl_compute_flags(sl_grid *grid, const void *const *fields, uint8_t *flags_out, void *stream);
 
