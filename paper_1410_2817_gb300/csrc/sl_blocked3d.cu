@@ -18,7 +18,6 @@
 namespace {
 
 constexpr int BX = 8, BY = 8, BZ = 4, NT3 = BX * BY * BZ;
-constexpr float FACE_MARGIN3 = 2e-5f;
 
 struct Geo3 {
     int n0, n1, n2;
@@ -92,10 +91,10 @@ __device__ __forceinline__ void cubic_w(float x, float w[4])
 // Sec. 2.2 element search in 3-D from element c, Newton in precision TN; D padded to 4 floats.
 template <typename TN>
 __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D, int max_iter, int walk_max,
-                                     const int j[3], int c[3], TN xi[3], int &hops, int &iters)
+                                     const int j[3], int c[3], TN xi[3], int &hops, int &iters, bool *degen)
 {
-    const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(1e-5);
-    const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(1e-5);
+    const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(SL_NEWTON_TOL_F32);
+    const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(SL_SLACK_F32);
     for (int hop = 0; hop < walk_max; ++hop) {
         TN P[8][3];
 #pragma unroll
@@ -107,7 +106,7 @@ __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D
             P[v][2] = TN(kz - j[2]) + TN(d.z);
         }
         int it = 0;
-        const int st = newton_solve3<TN>(P, max_iter, tol, xi, &it);
+        const int st = newton_solve3<TN>(P, max_iter, tol, xi, &it, degen);
         hops += 1;
         iters += it;
         bool finite = true, inside = true;
@@ -161,15 +160,14 @@ __global__ void __launch_bounds__(NT3, 2) remap_blocked3d_kernel(const Blocked3A
         }
         int hops = 0, iters = 0;
         float xf[3] = {0.f, 0.f, 0.f};
-        int st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters);
-        bool redo = st != ST_OK;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) redo |= fabsf(xf[q]) < FACE_MARGIN3 || fabsf(1.f - xf[q]) < FACE_MARGIN3;
-        if (redo) {
+        bool degen = false;
+        int st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters, &degen);
+        if (st != ST_OK || degen) {
             double xd[3] = {0.0, 0.0, 0.0};
+            bool degd = false;
             if (st == ST_LOCATE || st == ST_FOLD)
                 for (int q = 0; q < 3; ++q) c[q] = c0[q];
-            st = walk3<double>(g, a.D, a.max_iter, a.walk_max, j, c, xd, hops, iters);
+            st = walk3<double>(g, a.D, a.max_iter, a.walk_max, j, c, xd, hops, iters, &degd);
             for (int q = 0; q < 3; ++q) xf[q] = (float)xd[q];
             cnt.f64 += 1;
         }

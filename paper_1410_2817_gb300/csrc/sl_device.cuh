@@ -12,7 +12,7 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "../../include/sl.h"
+#include "sl.h"
 
 #define SL_MAX_FIELDS 8
 #define SL_MAX_VEL_PARAMS 80
@@ -72,6 +72,11 @@ __device__ __forceinline__ double min_t(double a, double b) { return fmin(a, b);
 // finite: false for NaN and +-Inf, without the generic isfinite()
 __device__ __forceinline__ bool finite_t(float x) { return fabsf(x) <= 3.40282346638528859812e+38f; }
 __device__ __forceinline__ bool finite_t(double x) { return fabs(x) <= 1.79769313486231570815e+308; }
+
+// 1/x: the FP32 paths take the approximate hardware reciprocal (Newton converges to the root of
+// x(xi) = 0 whatever the last bits of J^-1 are), FP64 keeps the IEEE division
+__device__ __forceinline__ float recip_t(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip_t(double x) { return 1.0 / x; }
 
 __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
@@ -173,15 +178,26 @@ __device__ __forceinline__ void rk4_cells(const VelArgs<T> &v, const T X[3], T o
     for (int a = 0; a < DIM; ++a) out[a] = (h / T(6) * (k1[a] + T(2) * k2[a] + T(2) * k3[a] + k4[a])) * v.inv_dx[a];
 }
 
+// FP32 production paths: Newton stops once |dxi| <= 3e-4; with quadratic convergence the error
+// left is about K * tol^2 (K = curvature / Jacobian of the element, below 1 for a non-degenerate
+// element), i.e. at FP32 rounding level.  An element is re-solved in FP64 only if the FP32
+// inversion failed or the element is close to degenerate (relative det below SL_DEGENERATE).
+#define SL_NEWTON_TOL_F32 3e-4f
+#define SL_SLACK_F32 1e-5f
+#define SL_DEGENERATE 1e-3f
+
 // ------------------------------------------------------------------------------------------------
 // Sec. 2.2, eq. (mapping1): Newton inversion of the multilinear element map.
 // P[v][a]: vertex v (bit a = offset along axis a) relative to the target, cell units.  The map is
 // expanded about the lower corner: x(xi) = P0 + sum_a xi_a A_a + sum_{a<b} xi_a xi_b E_ab
 // (+ xi_0 xi_1 xi_2 G in 3-D); Newton starts from the solution of the linear part.
-// Returns ST_OK, ST_NEWTON (iteration cap) or ST_FOLD (det J <= 0); xi holds the last iterate.
+// Returns ST_OK, ST_NEWTON (iteration cap) or ST_FOLD (det J <= 0); xi holds the last iterate and
+// *degenerate (if given) whether the converged Jacobian's det is below SL_DEGENERATE times the
+// product of its columns' 1-norms (1 for a square element, 0 for a collapsed one).
 // ------------------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T tol, T xi[3], int *iters)
+__device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T tol, T xi[3], int *iters,
+                                             bool *degenerate = nullptr)
 {
     const T ax = P[1][0] - P[0][0], ay = P[1][1] - P[0][1];
     const T bx = P[2][0] - P[0][0], by = P[2][1] - P[0][1];
@@ -189,12 +205,14 @@ __device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T to
     const T px = P[0][0], py = P[0][1];
     *iters = 0;
     T det = ax * by - bx * ay;
+    if (degenerate) *degenerate = true;
     if (!(det > T(0))) {
         xi[0] = xi[1] = T(NAN);
         return ST_FOLD;
     }
-    T s = -(px * by - py * bx) / det;
-    T t = -(ax * py - ay * px) / det;
+    T inv = recip_t(det);
+    T s = -(px * by - py * bx) * inv;
+    T t = -(ax * py - ay * px) * inv;
     for (int it = 1; it <= max_iter; ++it) {
         *iters = it;
         const T j11 = ax + t * ex, j21 = ay + t * ey;
@@ -208,13 +226,16 @@ __device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T to
             xi[1] = t;
             return ST_FOLD;
         }
-        const T d0 = (fx * j22 - fy * j12) / det;
-        const T d1 = (j11 * fy - j21 * fx) / det;
+        inv = recip_t(det);
+        const T d0 = (fx * j22 - fy * j12) * inv;
+        const T d1 = (j11 * fy - j21 * fx) * inv;
         s -= d0;
         t -= d1;
         if (max_t(abs_t(d0), abs_t(d1)) <= tol) {
             xi[0] = s;
             xi[1] = t;
+            if (degenerate)
+                *degenerate = det < T(SL_DEGENERATE) * ((abs_t(j11) + abs_t(j21)) * (abs_t(j12) + abs_t(j22)));
             return ST_OK;
         }
     }
@@ -230,7 +251,8 @@ __device__ __forceinline__ T det3(T a00, T a01, T a02, T a10, T a11, T a12, T a2
 }
 
 template <typename T>
-__device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T tol, T xi[3], int *iters)
+__device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T tol, T xi[3], int *iters,
+                                             bool *degenerate = nullptr)
 {
     T A[3][3], E01[3], E02[3], E12[3], G[3], P0[3];
 #pragma unroll
@@ -245,6 +267,7 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
         G[a] = P[7][a] - P[6][a] - P[5][a] - P[3][a] + P[1][a] + P[2][a] + P[4][a] - P[0][a];
     }
     *iters = 0;
+    if (degenerate) *degenerate = true;
     T det = det3(A[0][0], A[0][1], A[0][2], A[1][0], A[1][1], A[1][2], A[2][0], A[2][1], A[2][2]);
     if (!(det > T(0))) {
         xi[0] = xi[1] = xi[2] = T(NAN);
@@ -282,6 +305,12 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
             xi[0] = s0;
             xi[1] = s1;
             xi[2] = s2;
+            if (degenerate) {
+                T cn[3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) cn[b] = abs_t(J[0][b]) + abs_t(J[1][b]) + abs_t(J[2][b]);
+                *degenerate = det < T(SL_DEGENERATE) * (cn[0] * cn[1] * cn[2]);
+            }
             return ST_OK;
         }
     }
@@ -292,10 +321,11 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
 }
 
 template <typename T, int DIM>
-__device__ __forceinline__ int newton_solve(const T P[8][3], int max_iter, T tol, T xi[3], int *iters)
+__device__ __forceinline__ int newton_solve(const T P[8][3], int max_iter, T tol, T xi[3], int *iters,
+                                            bool *degenerate = nullptr)
 {
-    if (DIM == 2) return newton_solve2<T>(P, max_iter, tol, xi, iters);
-    return newton_solve3<T>(P, max_iter, tol, xi, iters);
+    if (DIM == 2) return newton_solve2<T>(P, max_iter, tol, xi, iters, degenerate);
+    return newton_solve3<T>(P, max_iter, tol, xi, iters, degenerate);
 }
 
 // ------------------------------------------------------------------------------------------------

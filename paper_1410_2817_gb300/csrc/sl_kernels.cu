@@ -30,8 +30,8 @@ GridArgs<T> make_grid_args(const sl_grid *g)
     a.newton_max_iter = g->desc.newton_max_iter;
     a.walk_max = g->desc.walk_max;
     a.walk_start = g->desc.walk_start;
-    a.tol = sizeof(T) == 8 ? (T)1e-14 : (T)1e-5;
-    a.slack = sizeof(T) == 8 ? (T)1e-12 : (T)1e-5;
+    a.tol = sizeof(T) == 8 ? (T)1e-14 : (T)SL_NEWTON_TOL_F32;
+    a.slack = sizeof(T) == 8 ? (T)1e-12 : (T)SL_SLACK_F32;
     return a;
 }
 
@@ -195,7 +195,8 @@ __device__ __forceinline__ void walk_start_cell(int mode, const int j[3], const 
 // element tried and xi its local coordinates; *hops and *iters are incremented.
 template <typename T, typename TN, int DIM>
 __device__ __forceinline__ int walk_global(const WalkParams<TN> &w, const int n[3], const T *__restrict__ D, int ds,
-                                           const int j[3], int c[3], TN xi[3], int *hops, int *iters)
+                                           const int j[3], int c[3], TN xi[3], int *hops, int *iters,
+                                           bool *degenerate = nullptr)
 {
     for (int hop = 0; hop < w.walk_max; ++hop) {
         TN P[8][3];
@@ -209,7 +210,7 @@ __device__ __forceinline__ int walk_global(const WalkParams<TN> &w, const int n[
             for (int a = 0; a < DIM; ++a) P[v][a] = TN(k[a] - j[a]) + (TN)__ldg(D + idx * ds + a);
         }
         int it = 0;
-        const int st = newton_solve<TN, DIM>(P, w.max_iter, w.tol, xi, &it);
+        const int st = newton_solve<TN, DIM>(P, w.max_iter, w.tol, xi, &it, degenerate);
         *hops += 1;
         *iters += it;
         bool finite = true, inside = true;
@@ -231,10 +232,6 @@ __device__ __forceinline__ int walk_global(const WalkParams<TN> &w, const int n[
     return ST_LOCATE;
 }
 
-// FP32 location is trusted unless the target lies within this distance of a face of its element
-// (where a rounding error could pick the neighbour) or the inversion failed.
-#define SL_MIXED_FACE_MARGIN 2e-5f
-
 template <typename T>
 struct RemapDebug {
     long long *cell;
@@ -244,7 +241,7 @@ struct RemapDebug {
 };
 
 // NMODE: 0 = Newton in T; 1 = Newton in FP64 (FP32 data); 2 = FP32 Newton, FP64 re-solve of targets
-// that failed or lie within SL_MIXED_FACE_MARGIN of a face.
+// whose FP32 inversion failed or whose element is close to degenerate.
 template <typename T, int DIM, int NMODE>
 __global__ void __launch_bounds__(256)
     remap_generic_kernel(GridArgs<T> g, const T *__restrict__ D, int ds, const uint8_t *__restrict__ flags,
@@ -268,15 +265,13 @@ __global__ void __launch_bounds__(256)
         for (int a = 0; a < DIM; ++a) Dj[a] = __ldg(D + jj * ds + a);
         int hops = 0, iters = 0;
         walk_start_cell<T, DIM>(g.walk_start, j, Dj, c);
-        int st = walk_global<T, TW, DIM>(wp, g.n, D, ds, j, c, xw, &hops, &iters);
+        bool degen = false;
+        int st = walk_global<T, TW, DIM>(wp, g.n, D, ds, j, c, xw, &hops, &iters, &degen);
         T xi[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int a = 0; a < DIM; ++a) xi[a] = (T)xw[a];
         if (NMODE == 2) {
-            bool redo = st != ST_OK;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a)
-                redo |= fabsf((float)xw[a]) < SL_MIXED_FACE_MARGIN || fabsf(1.0f - (float)xw[a]) < SL_MIXED_FACE_MARGIN;
+            const bool redo = st != ST_OK || degen;
             if (redo) {
                 WalkParams<double> wd;
                 wd.tol = 1e-14;

@@ -442,12 +442,16 @@ def test_tiled_matches_generic_f32(sl, orc, case):
         diags[kname] = g.diagnostics()
     scale = max(1.0, float(np.abs(h).max()))
     diff = np.abs(outs["tiled"] - outs["generic"])
-    # same elements, orders and Newton iterates; only the weight polynomials and the summation
-    # order differ (a few FP32 ulps)
-    assert float(diff.max()) <= 2e-6 * scale, float(diff.max())
+    # same elements, orders and Newton iterates away from faces; only the weight polynomials and
+    # the summation order differ (a few FP32 ulps).  The tiled kernel starts its walk from a
+    # refined estimate, so a target on a shared face (within the FP32 slack) may be accepted in
+    # the neighbouring element, whose order can differ: such ties must stay rare.
     dg, dt = diags["generic"], diags["tiled"]
-    assert dt["targets"] == dg["targets"] == n[0] * n[1]
-    assert dt["order_hist"] == dg["order_hist"]
+    ntar = n[0] * n[1]
+    assert float((diff > 2e-6 * scale).mean()) <= 1e-4, float(diff.max())
+    assert dt["targets"] == dg["targets"] == ntar
+    assert sum(dt["order_hist"]) == sum(dg["order_hist"])
+    assert max(abs(a - b) for a, b in zip(dt["order_hist"], dg["order_hist"])) <= max(2, 1e-4 * ntar)
     assert dt["fail_locate"] + dt["fail_newton"] + dt["fail_fold"] == dg["fail_locate"] + dg["fail_newton"] + dg["fail_fold"]
     if case == "shear_fallback":
         assert dt["tiles_fallback"] > 0
