@@ -92,6 +92,7 @@ typedef struct {
     int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
     int walk_start;                 /* SL_START_BACKWARD (from j - D_j) or SL_START_PAPER (Sec. 2.2) */
     int kernel;                     /* SL_KERNEL_AUTO, SL_KERNEL_GENERIC or SL_KERNEL_TILED           */
+    int tile_config;                /* 2-D FP32 tiles: 0 default (= 1), 1: 32x32, 2: 32x16, 3: 64x16  */
 } sl_grid_desc;
 
 /* Counters accumulated on the device since creation or the last sl_reset_diagnostics. */
@@ -168,6 +169,38 @@ sl_status sl_moments(sl_grid *grid, const void *field, int pmax, double *host_ou
  * that first call before any stream capture. */
 sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], const double hi[3], int dtype,
                              const void *field, int pmax, double *host_out, void *stream);
+
+/* ---- Batches: many independent 2-D FP32 grids advanced together ---------------------------
+ * A batch advances count grids (created with sl_create_grid, 2-D, SL_F32, the same nfields <= 4,
+ * max_order <= 1, backward walk start) by the same number of steps with one persistent launch per
+ * step over a work-list of (grid, tile) items: each item is the single-grid tiled step of that
+ * tile (Sec. 2.1-2.3, eq. multiZ, eq. vel).  Grids keep their own workspaces (displacements and
+ * counters).  The batch's device state (grid table, work-list, per-step work counters, grid
+ * times) lives in a caller-owned workspace of sl_batch_workspace_bytes() bytes (256-byte
+ * aligned); the library allocates no device memory. */
+typedef struct sl_batch sl_batch;
+
+/* Workspace bytes of a batch of these grids with tile configuration tile_config (0..3, as in
+ * sl_grid_desc); 0 if a grid is not eligible. */
+size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config);
+
+/* fields[q], scratch[q]: host arrays of nfields device planes of grid q (the planes are
+ * borrowed; scratch contents are undefined after a step).  t0[q], dt[q]: grid q's time and step.
+ * Copies the grid table to the device (synchronises).  Returns SL_ERR_UNSUPPORTED for
+ * ineligible grids and SL_ERR_NOMEM for a short workspace. */
+sl_status sl_batch_create(sl_grid *const *grids, int count, void *const *const *fields, void *const *const *scratch,
+                          const double *t0, const double *dt, int tile_config, void *dev_workspace, size_t ws_bytes,
+                          sl_batch **out);
+
+/* nsteps full steps of every grid (fields updated in place; each grid's time advances by
+ * nsteps*dt on the device).  use_graph != 0: the launch sequence of this step count is captured
+ * once into a CUDA graph and replayed (needs a non-NULL stream; make the first such call outside
+ * any other capture).  Calls on one batch must not overlap. */
+sl_status sl_batch_step(sl_batch *batch, int nsteps, int use_graph, void *stream);
+
+/* Work items per step, kernels launched so far, and the first grid's time (host mirror). */
+sl_status sl_batch_info(const sl_batch *batch, int *nitems, unsigned long long *launches, double *t_first);
+sl_status sl_batch_destroy(sl_batch *batch);
 
 /* Jump flags of Sec. 2.3 for `fields` into flags_out (device, N bytes; bit f for field f). */
 sl_status sl_compute_flags(sl_grid *grid, const void *const *fields, uint8_t *flags_out, void *stream);

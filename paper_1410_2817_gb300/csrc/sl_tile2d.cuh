@@ -1,0 +1,587 @@
+// sl_tile2d.cuh -- the per-tile body of the 2-D FP32 production kernels (single-grid and batched)
+// of the FSL step (arXiv:1410.2817).
+//
+// One CTA owns a TX x TY tile of target (reference) nodes.  Its targets' departure points lie
+// near j - D_j, so the CTA first takes the bounding box of the start elements floor(j - D_j),
+// widens it by the walk slack, the cubic stencil (Sec. 2.1: nodes c-1 .. c+2) and the limiter's
+// neighbours (Sec. 2.3), and stages that window -- displacements and field values -- in shared
+// memory with asynchronous copies.  The jump flags and their OR over every element's 4x4 stencil
+// are computed once per window node in shared memory, so each target's element search (Sec. 2.2),
+// order choice (Sec. 2.3) and tensor Z-spline sum (eq. multiZ) read shared memory only.  A target
+// whose walk leaves the window, or a tile whose window does not fit, falls back to global gathers.
+//
+// Precision: FP32 data and FP32 Newton; a target whose FP32 inversion failed, or whose element is
+// close to degenerate, is re-solved in FP64.  Up to four fields are interleaved per window node
+// (float4), so one 128-bit shared load serves every field of a stencil tap.
+//
+// The fused variant also integrates the next step's trajectories (eq. vel) for the tile's own
+// nodes: the velocity is given, so D(t + dt) does not depend on the fields being remapped.
+#pragma once
+
+#include <limits.h>
+#include <math.h>
+#include <string.h>
+
+#include "sl_internal.h"
+
+namespace {
+
+// Tile configuration: TX x TY targets per CTA of NT threads (TX a multiple of 32: one warp per
+// row segment), window capacity (TX + 2 HALO) x (TY + 2 HALO) nodes in shared memory.
+template <int TX_, int TY_, int NT_, int HALO_>
+struct TileCfg {
+    static constexpr int TX = TX_, TY = TY_, NT = NT_, HALO = HALO_;
+    static constexpr int ROWS = NT / TX;   // thread rows
+    static constexpr int TPT = TY / ROWS;  // targets per thread
+    static constexpr int WMAX = (TX + 2 * HALO) * (TY + 2 * HALO);
+    static_assert(TX % 32 == 0 && NT % TX == 0 && TY % ROWS == 0, "bad tile configuration");
+};
+typedef TileCfg<32, 32, 256, 8> CfgA;  // default
+typedef TileCfg<32, 16, 256, 8> CfgB;
+typedef TileCfg<64, 16, 256, 8> CfgC;
+
+constexpr int WALK_SLACK = 1;          // elements the walk may step beyond the start-cell box
+
+struct TileArgs {
+    int n0, n1;
+    int nfields, max_order;
+    float thr;
+    int max_iter, walk_max;
+    const float *D;
+    float *D_next;
+    const float *in[SL_MAX_FIELDS];
+    float *out[SL_MAX_FIELDS];
+    DevCounters *counters;
+};
+
+__device__ __forceinline__ int wrapi(int k, int n)
+{
+    int r = k % n;
+    return r < 0 ? r + n : r;
+}
+
+// wrap with a modulo only when k is outside [0, n)
+__device__ __forceinline__ int wrap_fast(int k, int n) { return (unsigned)k < (unsigned)n ? k : wrapi(k, n); }
+
+// start element floor(j - D_j), clamped so that garbage displacements cannot overflow the walk
+__device__ __forceinline__ int start_cell(int j, float d)
+{
+    const float s = fminf(fmaxf((float)j - d, (float)j - 65536.f), (float)j + 65536.f);
+    return finite_t(s) ? (int)floorf(s) : j;
+}
+
+__device__ __forceinline__ long long gidx(int x, int y, int n0, int n1)
+{
+    return (long long)wrap_fast(y, n1) * n0 + wrap_fast(x, n0);
+}
+
+// asynchronous global -> shared copies (LDGSTS); a CTA issues its whole window, then waits once
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// row of flat index q in a region `width` wide: (q + 0.5) / width in FP32 is exact enough to
+// floor correctly for q, width < 2^11 (the fractional part stays >= 0.5 / width)
+__device__ __forceinline__ int row_of(int q, float inv_width) { return __float2int_rz(((float)q + 0.5f) * inv_width); }
+
+// window geometry of one CTA
+struct Win {
+    int lox, loy, wx, wy;
+    __device__ __forceinline__ bool has(int x, int y) const
+    {
+        return (unsigned)(x - lox) < (unsigned)wx && (unsigned)(y - loy) < (unsigned)wy;
+    }
+    __device__ __forceinline__ int at(int x, int y) const { return (y - loy) * wx + (x - lox); }
+};
+
+// displacement of (unwrapped) node (x, y): shared memory when inside the window
+__device__ __forceinline__ float2 disp(const TileArgs &a, const Win &w, const float2 *sD, int x, int y)
+{
+    if (w.has(x, y)) return sD[w.at(x, y)];
+    return __ldg(reinterpret_cast<const float2 *>(a.D) + gidx(x, y, a.n0, a.n1));
+}
+
+// Sec. 2.2 element search from element (cx, cy) with Newton in precision TN (window wx = 0 when
+// nothing is staged, so every vertex then comes from global memory).
+template <typename TN>
+__device__ __forceinline__ int walk2(const TileArgs &a, const Win &w, const float2 *sD, int jx, int jy, int &cx,
+                                     int &cy, TN xi[3], int &hops, int &iters, bool &degen)
+{
+    const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(SL_NEWTON_TOL_F32);
+    const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(SL_SLACK_F32);
+    for (int hop = 0; hop < a.walk_max; ++hop) {
+        TN P[8][3];
+        float2 d4[4];
+        if (w.has(cx, cy) && w.has(cx + 1, cy + 1)) {
+            const int i0 = w.at(cx, cy);
+            d4[0] = sD[i0];
+            d4[1] = sD[i0 + 1];
+            d4[2] = sD[i0 + w.wx];
+            d4[3] = sD[i0 + w.wx + 1];
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) d4[v] = disp(a, w, sD, cx + (v & 1), cy + (v >> 1));
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            P[v][0] = TN(cx + (v & 1) - jx) + TN(d4[v].x);
+            P[v][1] = TN(cy + (v >> 1) - jy) + TN(d4[v].y);
+        }
+        int it = 0;
+        const int st = newton_solve2<TN>(P, a.max_iter, tol, xi, &it, &degen);
+        hops += 1;
+        iters += it;
+        if (!(finite_t(xi[0]) && finite_t(xi[1]))) return st == ST_OK ? ST_NEWTON : st;
+        const bool inside = xi[0] >= -slack && xi[0] <= TN(1) + slack && xi[1] >= -slack && xi[1] <= TN(1) + slack;
+        if (inside) return st;
+        if (xi[0] < -slack)
+            cx -= 1;
+        else if (xi[0] > TN(1) + slack)
+            cx += 1;
+        if (xi[1] < -slack)
+            cy -= 1;
+        else if (xi[1] > TN(1) + slack)
+            cy += 1;
+    }
+    return ST_LOCATE;
+}
+
+// FP64 re-solve of a target whose FP32 inversion failed or whose element is nearly degenerate
+// (rare: kept out of line so that it costs the main path no registers)
+__device__ __noinline__ int resolve_f64(const TileArgs &a, const Win &w, const float2 *sD, int jx, int jy, int st32,
+                                        int c0x, int c0y, int &ex, int &ey, float &xi0, float &xi1, int &hops,
+                                        int &iters)
+{
+    if (st32 == ST_LOCATE || st32 == ST_FOLD) {
+        ex = c0x;
+        ey = c0y;
+    }
+    double xd[3] = {0.0, 0.0, 0.0};
+    bool degen = false;
+    const int st = walk2<double>(a, w, sD, jx, jy, ex, ey, xd, hops, iters, degen);
+    xi0 = (float)xd[0];
+    xi1 = (float)xd[1];
+    return st;
+}
+
+// Sec. 2.3 flags of one node from global memory (fallback path)
+__device__ __forceinline__ unsigned node_flags_global(const TileArgs &a, int x, int y)
+{
+    unsigned bits = 0;
+    const long long c = gidx(x, y, a.n0, a.n1);
+    const long long xm = gidx(x - 1, y, a.n0, a.n1), xp = gidx(x + 1, y, a.n0, a.n1);
+    const long long ym = gidx(x, y - 1, a.n0, a.n1), yp = gidx(x, y + 1, a.n0, a.n1);
+    for (int f = 0; f < a.nfields; ++f) {
+        const float *h = a.in[f];
+        const float h0 = __ldg(h + c);
+        const bool hit = jump_test<float>(__ldg(h + xm), h0, __ldg(h + xp), a.thr) ||
+                         jump_test<float>(__ldg(h + ym), h0, __ldg(h + yp), a.thr);
+        bits |= hit ? (1u << f) : 0u;
+    }
+    return bits;
+}
+
+// order flags of element (ex, ey) from global memory: OR over its 4x4 stencil
+__device__ __noinline__ unsigned box_flags_global(const TileArgs &a, int ex, int ey)
+{
+    unsigned bits = 0;
+    for (int q = 0; q < 16; ++q) bits |= node_flags_global(a, ex - 1 + (q & 3), ey - 1 + (q >> 2));
+    return bits;
+}
+
+// Z~1 weights of taps c-1 .. c+2 at local coordinate x (Appendix)
+__device__ __forceinline__ void cubic_weights(float x, float w[4])
+{
+    const float y = 1.f - x, x2 = x * x, y2 = y * y;
+    w[0] = -0.5f * x * y2;
+    w[1] = fmaf(x2, fmaf(1.5f, x, -2.5f), 1.f);
+    w[2] = fmaf(y2, fmaf(1.5f, y, -2.5f), 1.f);
+    w[3] = -0.5f * x2 * y;
+}
+
+// eq. (multiZ) from global memory for a target whose stencil leaves the window
+__device__ __noinline__ void interp_global(const TileArgs &a, long long jj, int ex, int ey, float xi0, float xi1,
+                                           unsigned lin_mask)
+{
+    float wc[2][4];
+    cubic_weights(xi0, wc[0]);
+    cubic_weights(xi1, wc[1]);
+    for (int f = 0; f < a.nfields; ++f) {
+        const float *h = a.in[f];
+        float cub = 0.f, lin = 0.f;
+        for (int ky = 0; ky < 4; ++ky) {
+            float r = 0.f;
+            for (int kx = 0; kx < 4; ++kx) r = fmaf(wc[0][kx], __ldg(h + gidx(ex - 1 + kx, ey - 1 + ky, a.n0, a.n1)), r);
+            cub = fmaf(wc[1][ky], r, cub);
+        }
+        for (int ky = 0; ky < 2; ++ky) {
+            const float r = fmaf(xi0, __ldg(h + gidx(ex + 1, ey + ky, a.n0, a.n1)),
+                                 (1.f - xi0) * __ldg(h + gidx(ex, ey + ky, a.n0, a.n1)));
+            lin = fmaf(ky ? xi1 : 1.f - xi1, r, lin);
+        }
+        a.out[f][jj] = ((lin_mask >> f) & 1u) ? lin : cub;
+    }
+}
+
+// w * v + acc on the first NC components (the others are left as they are)
+template <int NC>
+__device__ __forceinline__ float4 fma4(float w, const float4 &v, const float4 &acc)
+{
+    return make_float4(fmaf(w, v.x, acc.x), NC > 1 ? fmaf(w, v.y, acc.y) : acc.y, NC > 2 ? fmaf(w, v.z, acc.z) : acc.z,
+                       NC > 3 ? fmaf(w, v.w, acc.w) : acc.w);
+}
+
+template <int NC>
+__device__ __forceinline__ float4 mul4(float w, const float4 &v)
+{
+    return make_float4(w * v.x, NC > 1 ? w * v.y : 0.f, NC > 2 ? w * v.z : 0.f, NC > 3 ? w * v.w : 0.f);
+}
+
+__device__ __forceinline__ float comp(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+
+// jump bits (Sec. 2.3) of the first NC fields interleaved in a float4
+template <int NC>
+__device__ __forceinline__ unsigned jump4(const float4 &m, const float4 &c, const float4 &p, float thr)
+{
+    unsigned b = 0;
+    b |= jump_test<float>(m.x, c.x, p.x, thr) ? 1u : 0u;
+    if (NC > 1) b |= jump_test<float>(m.y, c.y, p.y, thr) ? 2u : 0u;
+    if (NC > 2) b |= jump_test<float>(m.z, c.z, p.z, thr) ? 4u : 0u;
+    if (NC > 3) b |= jump_test<float>(m.w, c.w, p.w, thr) ? 8u : 0u;
+    return b;
+}
+
+__host__ __device__ constexpr int groups(int nf) { return (nf + 3) / 4; }
+__host__ __device__ constexpr int in_group(int nf, int g) { return nf - 4 * g < 4 ? nf - 4 * g : 4; }
+
+// eq. (multiZ) for the fields of group G (4 per float4) from the 4x4 taps starting at h: the cubic
+// (Z~1) sum and the bilinear (Z~0) sum over the element's own 4 vertices; fields whose lin_mask bit
+// is set take the bilinear value.
+template <int NF, int G>
+__device__ __forceinline__ void store_group(const TileArgs &a, long long jj, const float4 *h, int stride,
+                                            const float wc[2][4], float xi0, float xi1, unsigned lin_mask)
+{
+    constexpr int NC = in_group(NF, G);
+    float4 cub = make_float4(0.f, 0.f, 0.f, 0.f), lin = cub;
+#pragma unroll
+    for (int ky = 0; ky < 4; ++ky) {
+        const float4 t0 = h[0], t1 = h[1], t2 = h[2], t3 = h[3];
+        float4 r = mul4<NC>(wc[0][0], t0);
+        r = fma4<NC>(wc[0][1], t1, r);
+        r = fma4<NC>(wc[0][2], t2, r);
+        r = fma4<NC>(wc[0][3], t3, r);
+        cub = fma4<NC>(wc[1][ky], r, cub);
+        if (ky == 1 || ky == 2) lin = fma4<NC>(ky == 1 ? 1.f - xi1 : xi1, fma4<NC>(xi0, t2, mul4<NC>(1.f - xi0, t1)), lin);
+        h += stride;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int f = 4 * G + c;
+        a.out[f][jj] = ((lin_mask >> f) & 1u) ? comp(lin, c) : comp(cub, c);
+    }
+}
+
+// Shared memory of one tile: displacements, fields (4 per float4), flags, row-OR, box-OR.
+template <int NF, int WMAX>
+struct TileSmem {
+    float2 *D;
+    float4 *H;
+    uint8_t *F, *R, *B;
+    __device__ __forceinline__ explicit TileSmem(unsigned char *base)
+    {
+        D = reinterpret_cast<float2 *>(base);
+        H = reinterpret_cast<float4 *>(D + WMAX);
+        F = reinterpret_cast<uint8_t *>(H + groups(NF) * WMAX);
+        R = F + WMAX;
+        B = R + WMAX;
+    }
+};
+
+// One TX x TY tile of targets with origin (x0, y0): every thread of the CTA calls this; it
+// synchronises the CTA.
+template <class Cfg, int NF, bool FUSED>
+__device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0,
+                                             const TileSmem<NF, Cfg::WMAX> &sm, int *sBox, LocalCounters &cnt)
+{
+    constexpr int TX = Cfg::TX, NT = Cfg::NT, ROWS = Cfg::ROWS, TPT = Cfg::TPT, WMAX = Cfg::WMAX;
+    constexpr int NG = groups(NF);
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int n0 = a.n0, n1 = a.n1;
+    if (threadIdx.x < 4) sBox[threadIdx.x] = (threadIdx.x < 2) ? INT_MAX : INT_MIN;
+
+    // ---- phase 1: start elements floor(j - D_j) and their bounding box ----------------------
+    float sx[TPT], sy[TPT];
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
+        sx[k] = (float)jx;
+        sy[k] = (float)jy;
+        if (jx < n0 && jy < n1) {
+            const float2 d = __ldg(reinterpret_cast<const float2 *>(a.D) + (long long)jy * n0 + jx);
+            const float ux = fminf(fmaxf((float)jx - d.x, (float)jx - 65536.f), (float)jx + 65536.f);
+            const float uy = fminf(fmaxf((float)jy - d.y, (float)jy - 65536.f), (float)jy + 65536.f);
+            sx[k] = finite_t(ux) ? ux : (float)jx;
+            sy[k] = finite_t(uy) ? uy : (float)jy;
+            const int c0x = (int)floorf(sx[k]), c0y = (int)floorf(sy[k]);
+            mnx = min(mnx, c0x);
+            mny = min(mny, c0y);
+            mxx = max(mxx, c0x);
+            mxy = max(mxy, c0y);
+        }
+    }
+    __syncthreads();
+    mnx = __reduce_min_sync(0xffffffffu, mnx);
+    mny = __reduce_min_sync(0xffffffffu, mny);
+    mxx = __reduce_max_sync(0xffffffffu, mxx);
+    mxy = __reduce_max_sync(0xffffffffu, mxy);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&sBox[0], mnx);
+        atomicMin(&sBox[1], mny);
+        atomicMax(&sBox[2], mxx);
+        atomicMax(&sBox[3], mxy);
+    }
+    __syncthreads();
+    // window: start-cell box widened by the walk slack, the cubic stencil (c-1 .. c+2) and the
+    // limiter's neighbours (one more node each side)
+    Win w;
+    const long long wxl = (long long)sBox[2] - sBox[0] + 2 * WALK_SLACK + 6;
+    const long long wyl = (long long)sBox[3] - sBox[1] + 2 * WALK_SLACK + 6;
+    const bool staged = wxl > 0 && wyl > 0 && wxl <= WMAX && wyl <= WMAX && wxl * wyl <= WMAX;
+    w.lox = staged ? sBox[0] - WALK_SLACK - 2 : 0;
+    w.loy = staged ? sBox[1] - WALK_SLACK - 2 : 0;
+    w.wx = staged ? (int)wxl : 0;
+    w.wy = staged ? (int)wyl : 0;
+    const bool limit = a.max_order >= 1 && a.thr >= 0.f;
+
+    // ---- phase 2: stage displacements and fields of the window (all copies in flight) -------
+    const int nwin = w.wx * w.wy;
+    const float inv_wx = staged ? 1.f / (float)w.wx : 0.f;
+    for (int q = threadIdx.x; q < nwin; q += NT) {
+        const int wy = row_of(q, inv_wx), wx = q - wy * w.wx;
+        const long long gi = (long long)wrap_fast(w.loy + wy, n1) * n0 + wrap_fast(w.lox + wx, n0);
+        cp_async<8>(sm.D + q, reinterpret_cast<const float2 *>(a.D) + gi);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cp_async<4>(reinterpret_cast<float *>(sm.H + (f >> 2) * WMAX + q) + (f & 3), a.in[f] + gi);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // ---- phase 3: jump flags (Sec. 2.3) and their OR over each element's 4x4 stencil ---------
+    if (limit) {
+        // flags of the interior nodes (the limiter needs both neighbours on each axis)
+        const int iw = w.wx - 2, ni = iw * (w.wy - 2);
+        const float inv_iw = 1.f / (float)max(iw, 1);
+        for (int q = threadIdx.x; q < ni; q += NT) {
+            const int r = row_of(q, inv_iw);
+            const int idx = (r + 1) * w.wx + (q - r * iw) + 1;
+            unsigned bits = 0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const float4 *h = sm.H + g * WMAX;
+                const float4 c = h[idx];
+                if (in_group(NF, g) == 4)
+                    bits |= (jump4<4>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<4>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                            << (4 * g);
+                else if (in_group(NF, g) == 3)
+                    bits |= (jump4<3>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<3>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                            << (4 * g);
+                else if (in_group(NF, g) == 2)
+                    bits |= (jump4<2>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<2>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                            << (4 * g);
+                else
+                    bits |= (jump4<1>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<1>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                            << (4 * g);
+            }
+            sm.F[idx] = (uint8_t)bits;
+        }
+        __syncthreads();
+        // OR along x over c-1 .. c+2 for rows 1 .. wy-2, columns 2 .. wx-4
+        const int rw = w.wx - 5, nr = rw * (w.wy - 2);
+        const float inv_rw = 1.f / (float)max(rw, 1);
+        for (int q = threadIdx.x; q < nr; q += NT) {
+            const int r = row_of(q, inv_rw);
+            const int idx = (r + 1) * w.wx + (q - r * rw) + 2;
+            sm.R[idx] = sm.F[idx - 1] | sm.F[idx] | sm.F[idx + 1] | sm.F[idx + 2];
+        }
+        __syncthreads();
+        // OR along y: the element's 4x4 stencil, rows 2 .. wy-4
+        const int nb = rw * (w.wy - 5);
+        for (int q = threadIdx.x; q < nb; q += NT) {
+            const int r = row_of(q, inv_rw);
+            const int idx = (r + 2) * w.wx + (q - r * rw) + 2;
+            sm.B[idx] = sm.R[idx - w.wx] | sm.R[idx] | sm.R[idx + w.wx] | sm.R[idx + 2 * w.wx];
+        }
+        __syncthreads();
+    }
+
+    // ---- phase 4: per target: search, Newton, order, tensor Z-spline sum ---------------------
+    if (!staged && threadIdx.x == 0) cnt.fallback += 1;
+#pragma unroll 1
+    for (int k = 0; k < TPT; ++k) {
+        const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
+        if (jx >= n0 || jy >= n1) continue;
+        const long long jj = (long long)jy * n0 + jx;
+        // start element: one fixed-point step s <- j - D(s) from s0 = j - D_j, with D(s0)
+        // interpolated bilinearly in the staged window (the walk below still decides)
+        int ex = (int)floorf(sx[k]), ey = (int)floorf(sy[k]);
+        const int c0x = ex, c0y = ey;
+        if (staged) {
+            const int i0 = w.at(ex, ey);
+            const float fx = sx[k] - (float)ex, fy = sy[k] - (float)ey;
+            const float2 d00 = sm.D[i0], d10 = sm.D[i0 + 1], d01 = sm.D[i0 + w.wx], d11 = sm.D[i0 + w.wx + 1];
+            const float dx = fmaf(fy, fmaf(fx, d11.x - d01.x, d01.x) - fmaf(fx, d10.x - d00.x, d00.x), fmaf(fx, d10.x - d00.x, d00.x));
+            const float dy = fmaf(fy, fmaf(fx, d11.y - d01.y, d01.y) - fmaf(fx, d10.y - d00.y, d00.y), fmaf(fx, d10.y - d00.y, d00.y));
+            const float rx_ = (float)jx - dx, ry_ = (float)jy - dy;
+            if (finite_t(rx_) && finite_t(ry_) && fabsf(rx_ - sx[k]) < 4.f && fabsf(ry_ - sy[k]) < 4.f) {
+                ex = (int)floorf(rx_);
+                ey = (int)floorf(ry_);
+            }
+        }
+        int hops = 0, iters = 0;
+        float xf[3] = {0.f, 0.f, 0.f};
+        bool degen = false;
+        int st = walk2<float>(a, w, sm.D, jx, jy, ex, ey, xf, hops, iters, degen);
+        float xi0 = xf[0], xi1 = xf[1];
+        if (st != ST_OK || degen) {
+            st = resolve_f64(a, w, sm.D, jx, jy, st, c0x, c0y, ex, ey, xi0, xi1, hops, iters);
+            cnt.f64 += 1;
+        }
+        cnt.targets += 1;
+        cnt.hops += hops;
+        cnt.hops_max = max(cnt.hops_max, (unsigned)hops);
+        cnt.iters += iters;
+        cnt.iters_max = max(cnt.iters_max, (unsigned)iters);
+        if (st != ST_OK) {
+            cnt.fl += st == ST_LOCATE;
+            cnt.fn += st == ST_NEWTON;
+            cnt.ff += st == ST_FOLD;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a.out[f][jj] = __ldg(a.in[f] + jj);
+        } else {
+            const int rx = ex - w.lox, ry = ey - w.loy;
+            const bool fast = rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;  // false when not staged
+            // Sec. 2.3: fields flagged anywhere in the element's 4x4 stencil drop to linear
+            unsigned lin_mask = a.max_order == 0 ? 0xffu : 0u;
+            if (limit) lin_mask = fast ? (unsigned)sm.B[ry * w.wx + rx] : box_flags_global(a, ex, ey);
+            const unsigned nlin = __popc(lin_mask & ((1u << NF) - 1u));
+            cnt.oh0 += nlin;
+            cnt.oh1 += NF - nlin;
+            if (fast) {
+                float wc[2][4];
+                cubic_weights(xi0, wc[0]);
+                cubic_weights(xi1, wc[1]);
+                const int o = (ry - 1) * w.wx + (rx - 1);
+                store_group<NF, 0>(a, jj, sm.H + o, w.wx, wc, xi0, xi1, lin_mask);
+                if constexpr (NG > 1) store_group<NF, 1>(a, jj, sm.H + WMAX + o, w.wx, wc, xi0, xi1, lin_mask);
+            } else {
+                interp_global(a, jj, ex, ey, xi0, xi1, lin_mask);
+            }
+        }
+        if (FUSED && a.D_next != nullptr) {
+            float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
+            rk4_cells<float, 2>(vn, X, d);
+            reinterpret_cast<float2 *>(a.D_next)[jj] = make_float2(d[0], d[1]);
+        }
+    }
+}
+
+template <class Cfg, int NF, bool FUSED>
+__global__ void __launch_bounds__(Cfg::NT, 3) remap_tiled2d_kernel(const TileArgs a, const VelArgs<float> vn)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sBox[4];
+    const TileSmem<NF, Cfg::WMAX> sm(smem);
+    LocalCounters cnt;
+    cnt.clear();
+    process_tile<Cfg, NF, FUSED>(a, vn, blockIdx.x * Cfg::TX, blockIdx.y * Cfg::TY, sm, sBox, cnt);
+    flush_counters(cnt, a.counters);
+}
+
+template <class Cfg>
+__host__ size_t tile_smem_bytes(int nfields)
+{
+    return (size_t)Cfg::WMAX * (sizeof(float2) + sizeof(float4) * (size_t)((nfields + 3) / 4) + 3);
+}
+
+__host__ inline TileArgs make_tile_args(const sl_grid *g, const void *D, void *D_next, const void *const *in,
+                                        void *const *out)
+{
+    TileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n0 = (int)g->n[0];
+    a.n1 = (int)g->n[1];
+    a.nfields = g->nfields;
+    a.max_order = g->desc.max_order;
+    a.thr = (float)g->desc.limiter_threshold;
+    a.max_iter = g->desc.newton_max_iter;
+    a.walk_max = g->desc.walk_max;
+    a.D = (const float *)D;
+    a.D_next = (float *)D_next;
+    for (int f = 0; f < g->nfields; ++f) {
+        a.in[f] = (const float *)in[f];
+        a.out[f] = (float *)out[f];
+    }
+    a.counters = g->counters;
+    return a;
+}
+
+// opt-in shared memory above 48 KB is a per-device function attribute: set it once per device
+template <class K>
+__host__ cudaError_t allow_smem(K kernel, int device, size_t bytes, bool *configured)
+{
+    if (!configured[device & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        configured[device & 63] = true;
+    }
+    return cudaSuccess;
+}
+
+template <class Cfg, int NF, bool FUSED>
+__host__ cudaError_t launch_tiled_nf(const sl_grid *g, const TileArgs &a, const VelArgs<float> &vn, cudaStream_t s)
+{
+    const size_t smem = tile_smem_bytes<Cfg>(NF);
+    static bool configured[64] = {};
+    cudaError_t e = allow_smem(remap_tiled2d_kernel<Cfg, NF, FUSED>, g->device, smem, configured);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g->n[0] + Cfg::TX - 1) / Cfg::TX), (unsigned)((g->n[1] + Cfg::TY - 1) / Cfg::TY));
+    remap_tiled2d_kernel<Cfg, NF, FUSED><<<grid, Cfg::NT, smem, s>>>(a, vn);
+    return cudaGetLastError();
+}
+
+template <class Cfg, bool FUSED>
+__host__ cudaError_t launch_tiled_fused(const sl_grid *g, const TileArgs &a, const VelArgs<float> &vn, cudaStream_t s)
+{
+    switch (g->nfields) {
+    case 1: return launch_tiled_nf<Cfg, 1, FUSED>(g, a, vn, s);
+    case 2: return launch_tiled_nf<Cfg, 2, FUSED>(g, a, vn, s);
+    case 3: return launch_tiled_nf<Cfg, 3, FUSED>(g, a, vn, s);
+    case 4: return launch_tiled_nf<Cfg, 4, FUSED>(g, a, vn, s);
+    case 5: return launch_tiled_nf<Cfg, 5, FUSED>(g, a, vn, s);
+    case 6: return launch_tiled_nf<Cfg, 6, FUSED>(g, a, vn, s);
+    case 7: return launch_tiled_nf<Cfg, 7, FUSED>(g, a, vn, s);
+    default: return launch_tiled_nf<Cfg, 8, FUSED>(g, a, vn, s);
+    }
+}
+
+// one tiled remap (fused: also D(t_next) for the tile's nodes) of a 2-D FP32 grid
+template <class Cfg>
+__host__ cudaError_t launch_tiled_cfg(const sl_grid *g, const void *D, void *D_next, double t_next, double dt,
+                                      bool fused, const void *const *in, void *const *out, cudaStream_t s)
+{
+    const TileArgs a = make_tile_args(g, D, D_next, in, out);
+    if (fused) {
+        const VelArgs<float> vn = make_vel_args<float>(g, t_next, dt);
+        return launch_tiled_fused<Cfg, true>(g, a, vn, s);
+    }
+    VelArgs<float> vn;
+    memset(&vn, 0, sizeof(vn));
+    return launch_tiled_fused<Cfg, false>(g, a, vn, s);
+}
+
+}  // namespace

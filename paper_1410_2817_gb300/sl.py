@@ -44,6 +44,7 @@ class sl_grid_desc(C.Structure):
         ("integrator", C.c_int), ("velocity_kind", C.c_int), ("velocity_params", C.POINTER(C.c_double)),
         ("n_velocity_params", C.c_int), ("newton_mode", C.c_int), ("newton_max_iter", C.c_int),
         ("walk_max", C.c_int), ("fail_policy", C.c_int), ("walk_start", C.c_int), ("kernel", C.c_int),
+        ("tile_config", C.c_int),
     ]
 
 
@@ -93,6 +94,12 @@ def lib():
             "sl_get_displacement": (C.c_int, [vp, vp, i64, vp]),
             "sl_get_diagnostics": (C.c_int, [vp, C.POINTER(sl_diag), vp]),
             "sl_reset_diagnostics": (C.c_int, [vp, vp]),
+            "sl_batch_workspace_bytes": (C.c_size_t, [C.POINTER(vp), C.c_int, C.c_int]),
+            "sl_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(pp), C.POINTER(pp), dp, dp, C.c_int, vp,
+                                          C.c_size_t, C.POINTER(vp)]),
+            "sl_batch_step": (C.c_int, [vp, C.c_int, C.c_int, vp]),
+            "sl_batch_info": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_ulonglong), dp]),
+            "sl_batch_destroy": (C.c_int, [vp]),
             "sl_status_string": (C.c_char_p, [C.c_int]),
             "sl_last_error": (C.c_char_p, []),
             "sl_version": (C.c_char_p, []),
@@ -135,7 +142,7 @@ def _planes(ts: Sequence[torch.Tensor]):
 def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), max_order=1,
               limiter_threshold=0.25, velocity="uniform", velocity_params=(0.0, 0.0, 0.0),
               newton_mode=None, newton_max_iter=0, walk_max=0, fail_policy=SL_FAIL_KEEP,
-              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO):
+              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO, tile_config=0):
     d = sl_grid_desc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -153,7 +160,7 @@ def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1
     if newton_mode is None:
         newton_mode = SL_NEWTON_MIXED if dtype == SL_F32 else SL_NEWTON_F64
     d.newton_mode, d.newton_max_iter, d.walk_max = newton_mode, newton_max_iter, walk_max
-    d.fail_policy, d.walk_start, d.kernel = fail_policy, walk_start, kernel
+    d.fail_policy, d.walk_start, d.kernel, d.tile_config = fail_policy, walk_start, kernel, tile_config
     return d
 
 
@@ -320,6 +327,59 @@ class Grid:
 
     def reset_diagnostics(self, stream=None):
         sl_reset_diagnostics(self.handle, stream)
+
+
+def sl_batch_workspace_bytes(grids: Sequence["Grid"], tile_config: int = 0) -> int:
+    arr = (C.c_void_p * len(grids))(*[g.handle.value for g in grids])
+    return int(lib().sl_batch_workspace_bytes(arr, len(grids), int(tile_config)))
+
+
+class Batch:
+    """Grids advanced together by sl_batch_step (one persistent launch per step).  fields[q] and
+    scratch[q] are (nfields, ny, nx) FP32 CUDA tensors of grid q."""
+
+    def __init__(self, grids: Sequence["Grid"], fields, scratch, t0, dt, tile_config: int = 0, device="cuda"):
+        self.grids = list(grids)
+        n = len(self.grids)
+        self._keep = []
+        arr = (C.c_void_p * n)(*[g.handle.value for g in self.grids])
+        fps = (C.POINTER(C.c_void_p) * n)()
+        sps = (C.POINTER(C.c_void_p) * n)()
+        for q in range(n):
+            pf, a = _planes(list(fields[q]))
+            ps, b = _planes(list(scratch[q]))
+            fps[q], sps[q] = pf, ps
+            self._keep += [a, b]
+        t0a = (C.c_double * n)(*[float(v) for v in t0])
+        dta = (C.c_double * n)(*[float(v) for v in dt])
+        nb = int(lib().sl_batch_workspace_bytes(arr, n, int(tile_config)))
+        if nb == 0:
+            raise SLError(SL_ERR_UNSUPPORTED, "Batch", "grids not eligible for a batch")
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=device)
+        h = C.c_void_p()
+        _check(lib().sl_batch_create(arr, n, fps, sps, t0a, dta, int(tile_config), C.c_void_p(self.workspace.data_ptr()),
+                                     nb, C.byref(h)), "sl_batch_create")
+        self.handle = h
+        self.fields, self.scratch = fields, scratch
+
+    def step(self, nsteps: int, use_graph: bool = False, stream=None):
+        _check(lib().sl_batch_step(self.handle, int(nsteps), 1 if use_graph else 0, _stream(stream)), "sl_batch_step")
+
+    def info(self):
+        ni, nl, t = C.c_int(), C.c_ulonglong(), C.c_double()
+        _check(lib().sl_batch_info(self.handle, C.byref(ni), C.byref(nl), C.byref(t)), "sl_batch_info")
+        return {"items": ni.value, "launches": nl.value, "t_first": t.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            lib().sl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def grid_for(workload, dtype=SL_F32, **kw) -> Grid:
