@@ -210,6 +210,61 @@ def kernel_only(args):
     return 0
 
 
+def batched_leg(torch, sl, inputs, steps=50, tile_config=0):
+    """512 independent 2-D grids (sides log-uniform in [32, 512], random Fourier streamfunctions,
+    Gaussian + step fields, FP32), all advanced 50 steps by one persistent launch per step under a
+    CUDA graph.  The working set (~0.8 GB) is larger than L2."""
+    wls = inputs.batched_grids(count=512, seed=0, steps=steps)
+    nodes = sum(wl.nnodes for wl in wls)
+    grids = [sl.grid_for(wl, sl.SL_F32, tile_config=tile_config) for wl in wls]
+    fields = [torch.tensor(wl.fields, dtype=torch.float32, device="cuda") for wl in wls]
+    scratch = [torch.empty_like(f) for f in fields]
+    stream = torch.cuda.Stream()
+    b = sl.Batch(grids, fields, scratch, [0.0] * len(wls), [wl.dt for wl in wls], tile_config=tile_config)
+    with torch.cuda.stream(stream):
+        b.step(steps, use_graph=True, stream=stream)  # capture + warm-up
+        b.step(steps, use_graph=True, stream=stream)
+        l0 = b.info()["launches"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps, use_graph=True, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    fails = sum(g.diagnostics()["fail_locate"] + g.diagnostics()["fail_fold"] + g.diagnostics()["fail_newton"]
+                for g in grids)
+    out = {"workload": "512 grids, sides 32-512 (seed 0), 2 fields, 50 steps, one graph replay",
+           "nodes": nodes, "value": nodes * steps / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
+           "launches_per_call": b.info()["launches"] - l0, "tile_config": tile_config, "failed_targets": fails}
+    b.close()
+    return out
+
+
+def deform3d_leg(torch, sl, inputs, steps=5):
+    """3-D 256^3 deformation flow (T = 3, dt = 0.03), two fields, FP32 bulk with FP64 re-solves of
+    degenerate elements: `steps` full steps through sl_step, L2 flushed before each."""
+    wl = inputs.workload_deform3d(256, steps=steps)
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    s = torch.empty_like(f)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    g.step(f, s, 0.0, wl.dt, 1)
+    ms = []
+    t = wl.dt
+    for k in range(steps):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(f, s, t, wl.dt, 1)
+        b.record()
+        ms.append((a, b))
+        t += wl.dt
+    torch.cuda.synchronize()
+    tot = sum(a.elapsed_time(b) for a, b in ms)
+    return {"workload": "deform3d 256^3, 2 fields, FP32", "value": wl.nnodes * steps / (tot * 1e-3), "unit": UNIT,
+            "ms_per_step": tot / steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,6 +273,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and 3-D legs")
     ap.add_argument("--mode", default="full", choices=["full", "remap", "step"],
                     help="remap/step: only launch that call --steps times (for profilers); prints its timing")
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
@@ -334,6 +390,9 @@ def main():
     e2e_value = ws * N * e2e_steps / (e2e_ms * 1e-3)
     plane_bytes = NFIELDS * N * 4
 
+    batched = batched_leg(torch, sl, inputs) if not args.no_extra else None
+    deform3d = deform3d_leg(torch, sl, inputs) if not args.no_extra else None
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -353,6 +412,8 @@ def main():
                      "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": remap_ms, "advect_ms": advect_ms},
         "cpu_baseline": cpu,
+        "batched": batched,
+        "deform3d_256": deform3d,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": plane_bytes, "d2h_bytes_per_step": plane_bytes},
         "gpu_launches": launches,
         "clocks": clocks,
