@@ -265,6 +265,23 @@ def deform3d_leg(torch, sl, inputs, steps=5):
             "ms_per_step": tot / steps}
 
 
+def serving_leg(njobs, budget_gb=120.0):
+    """The first `njobs` jobs of the served trace (Poisson arrivals, mean 200 jobs/s, seed 1; 70 %
+    2-D 64^2-2048^2, 30 % 3-D 32^3-192^3, 1-4 fields, 10-200 steps, 10 % FP64), served in real time
+    by the continuous-batching server under a 120 GB device-memory budget."""
+    from paper_1410_2817_gb300 import inputs, serve
+    jobs = inputs.serving_trace(njobs=njobs, seed=1)
+
+    def fields_of(job):
+        wl = job.workload
+        return inputs.job_fields_device(wl.dim, wl.n[0], wl.nfields, seed=1000 + job.job_id)
+
+    out = serve.serve_trace(jobs, fields_of, budget_bytes=int(budget_gb * (1 << 30)))
+    out.pop("results", None)
+    out["trace"] = f"first {njobs} jobs of serving_trace(seed=1)"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,7 +290,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched and 3-D legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched, 3-D and serving legs")
+    ap.add_argument("--serve-jobs", type=int, default=300, help="jobs of the served trace (0: skip)")
     ap.add_argument("--mode", default="full", choices=["full", "remap", "step"],
                     help="remap/step: only launch that call --steps times (for profilers); prints its timing")
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
@@ -392,6 +410,7 @@ def main():
 
     batched = batched_leg(torch, sl, inputs) if not args.no_extra else None
     deform3d = deform3d_leg(torch, sl, inputs) if not args.no_extra else None
+    serving = serving_leg(args.serve_jobs) if (not args.no_extra and args.serve_jobs > 0) else None
 
     if rank != 0:
         if dist is not None:
@@ -414,6 +433,7 @@ def main():
         "cpu_baseline": cpu,
         "batched": batched,
         "deform3d_256": deform3d,
+        "serving": serving,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": plane_bytes, "d2h_bytes_per_step": plane_bytes},
         "gpu_launches": launches,
         "clocks": clocks,

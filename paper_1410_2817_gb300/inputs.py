@@ -234,6 +234,23 @@ def job_fields(dim: int, n: int, nfields: int, seed: int) -> np.ndarray:
     return np.stack(planes)
 
 
+def job_fields_device(dim: int, n: int, nfields: int, seed: int, device="cuda", dtype=None):
+    """job_fields evaluated with torch on `device` (same seeded centres and shapes), so that a server
+    can create a large job's initial fields without stalling on the host."""
+    import torch
+    dtype = dtype or torch.float64
+    rng = np.random.default_rng(seed)
+    ax = torch.arange(n, device=device, dtype=torch.float64) / n
+    coords = torch.meshgrid(*([ax] * dim), indexing="ij")  # (z, y, x) order: x is the last axis
+    coords = list(reversed(coords))
+    planes = []
+    for f in range(nfields):
+        c = rng.uniform(0.2, 0.8, size=dim)
+        r2 = sum((coords[a] - c[a] - torch.round(coords[a] - c[a])) ** 2 for a in range(dim))
+        planes.append(torch.exp(-r2 / (2 * 0.1 ** 2)) if f % 2 == 0 else (r2 < 0.15 ** 2).to(torch.float64))
+    return torch.stack(planes).to(dtype)
+
+
 def serving_trace(njobs: int = 2000, seed: int = 1, rate_hz: float = 200.0, frac_3d: float = 0.3,
                   frac_f64: float = 0.1, side2d=(64, 2048), side3d=(32, 192), steps=(10, 200),
                   cfl: float = 4.0) -> List[Job]:
