@@ -265,12 +265,12 @@ def deform3d_leg(torch, sl, inputs, steps=5):
             "ms_per_step": tot / steps}
 
 
-def serving_leg(njobs, budget_gb=120.0):
+def serving_leg(njobs, rank=0, world=1, budget_gb=120.0):
     """The first `njobs` jobs of the served trace (Poisson arrivals, mean 200 jobs/s, seed 1; 70 %
     2-D 64^2-2048^2, 30 % 3-D 32^3-192^3, 1-4 fields, 10-200 steps, 10 % FP64), served in real time
     by the continuous-batching server under a 120 GB device-memory budget."""
     from paper_1410_2817_gb300 import inputs, serve
-    jobs = inputs.serving_trace(njobs=njobs, seed=1)
+    jobs = serve.shard_jobs(inputs.serving_trace(njobs=njobs, seed=1), rank, world)  # independent jobs
 
     def fields_of(job):
         wl = job.workload
@@ -410,7 +410,7 @@ def main():
 
     batched = batched_leg(torch, sl, inputs) if not args.no_extra else None
     deform3d = deform3d_leg(torch, sl, inputs) if not args.no_extra else None
-    serving = serving_leg(args.serve_jobs) if (not args.no_extra and args.serve_jobs > 0) else None
+    serving = serving_leg(args.serve_jobs, rank, ws) if (not args.no_extra and args.serve_jobs > 0) else None
 
     if rank != 0:
         if dist is not None:
