@@ -168,6 +168,9 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     g->D[0] = g->ws + L.D0;
     g->D[1] = g->ws + L.D1;
     g->dcur = 0;
+    const int vk = desc->velocity_kind;
+    g->steady = vk == SL_VEL_UNIFORM || vk == SL_VEL_SOLID_BODY || vk == SL_VEL_FOURIER2D || vk == SL_VEL_FOURIER3D;
+    g->d_cached = 0;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ws, 0, L.total, 0);
@@ -220,6 +223,8 @@ extern "C" sl_status sl_advect_nodes(sl_grid *g, double t, double dt, void *stre
     cudaError_t e = g->dtype == SL_F64 ? Launch<double>::advect(g, g->D[g->dcur], t, dt, s)
                                        : Launch<float>::advect(g, g->D[g->dcur], t, dt, s);
     e = counted(g, e, 1);
+    g->d_cached = e == cudaSuccess && g->steady;
+    g->d_cached_dt = dt;
     return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_advect_nodes");
 }
 
@@ -280,23 +285,36 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
     }
     cudaError_t e = cudaSuccess;
     const bool fused = use_tiled<T>(g);
-    if (fused) {
+    // steady velocity: one integration serves every step (and later calls with the same dt)
+    const bool reuse = g->steady != 0;
+    if (reuse && !(g->d_cached && g->d_cached_dt == dt)) {
+        e = counted(g, Launch<T>::advect(g, g->D[g->dcur], t0, dt, s), 1);
+        if (e != cudaSuccess) return e;
+        g->d_cached = 1;
+        g->d_cached_dt = dt;
+    }
+    if (fused && !reuse) {
         // the velocity is given, so D of the next step does not depend on the fields: each fused
         // launch remaps with D[cur] and writes D[next] for its own nodes
         e = counted(g, Launch<T>::advect(g, g->D[g->dcur], t0, dt, s), 1);
         if (e != cudaSuccess) return e;
+        g->d_cached = 0;
     }
     for (int k = 0; k < nsteps; ++k) {
         const double t = t0 + (double)k * dt;
         if (fused) {
             const int nx = g->dcur ^ 1;
-            e = counted(g, Launch<T>::step_fused(g, g->D[g->dcur], k + 1 < nsteps ? g->D[nx] : nullptr, t + dt, dt,
-                                                 cur, nxt, s), tiled_kernels_per_call(g));
+            void *dnext = (!reuse && k + 1 < nsteps) ? g->D[nx] : nullptr;
+            e = counted(g, Launch<T>::step_fused(g, g->D[g->dcur], dnext, t + dt, dt, cur, nxt, s),
+                        tiled_kernels_per_call(g));
             if (e != cudaSuccess) return e;
-            if (k + 1 < nsteps) g->dcur = nx;
+            if (dnext) g->dcur = nx;
         } else {
             e = counted(g, Launch<T>::flags(g, cur, g->flags, s), 1);
-            if (e == cudaSuccess) e = counted(g, Launch<T>::advect(g, g->D[g->dcur], t, dt, s), 1);
+            if (e == cudaSuccess && !reuse) {
+                e = counted(g, Launch<T>::advect(g, g->D[g->dcur], t, dt, s), 1);
+                g->d_cached = 0;
+            }
             if (e == cudaSuccess)
                 e = counted(g, Launch<T>::remap_generic(g, g->D[g->dcur], g->flags, cur, nxt, nullptr, s), 1);
             if (e != cudaSuccess) return e;
@@ -384,6 +402,7 @@ extern "C" sl_status sl_set_displacement(sl_grid *g, const void *D, int64_t stri
     cudaError_t e = g->dtype == SL_F64 ? Launch<double>::copy_disp(g, D, stride, g->D[g->dcur], g->ds, s)
                                        : Launch<float>::copy_disp(g, D, stride, g->D[g->dcur], g->ds, s);
     e = counted(g, e, 1);
+    g->d_cached = 0;  // a displacement set by the caller is not the velocity's
     return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_set_displacement");
 }
 

@@ -29,6 +29,7 @@ struct BatchGrid {
     float *D[2];
     double dt, period;             // period > 0: time-dependent velocity cos(pi t / period)
     int dcur;                      // displacement buffer holding D at the call's first step
+    int steady;                    // steady velocity: D of the first step serves every step
     int tiles_x, tile_base;
 };
 
@@ -84,8 +85,8 @@ __global__ void __launch_bounds__(Cfg::NT, 3)
                 sa.in[f] = even ? sg.fields[f] : sg.scratch[f];
                 sa.out[f] = even ? sg.scratch[f] : const_cast<float *>(sg.fields[f]);
             }
-            sa.D = sg.D[(sg.dcur + k) & 1];
-            sa.D_next = last ? nullptr : sg.D[(sg.dcur + k + 1) & 1];
+            sa.D = sg.steady ? sg.D[sg.dcur] : sg.D[(sg.dcur + k) & 1];
+            sa.D_next = (last || sg.steady) ? nullptr : sg.D[(sg.dcur + k + 1) & 1];
             sv = sg.vel;
             stage_factors(sg, tgrid[gid] + (double)(k + 1) * sg.dt, sv.ct);
         }
@@ -275,6 +276,7 @@ extern "C" sl_status sl_batch_create(sl_grid *const *grids, int count, void *con
         e.dt = dt[q];
         e.period = (g->desc.velocity_kind == SL_VEL_SWIRL2D) ? g->vel_params[0] : 0.0;
         e.dcur = g->dcur;
+        e.steady = g->steady;
         int tx, ty;
         tile_counts(tile_config, g, &tx, &ty);
         e.tiles_x = tx;
@@ -384,7 +386,8 @@ extern "C" sl_status sl_batch_step(sl_batch *b, int nsteps, int use_graph, void 
         // every call integrates D afresh into the table's starting buffer, so the table (and any
         // captured graph) never changes; the grid objects point at the last step's D
         for (int q = 0; q < b->count; ++q) {
-            b->grids[q]->dcur = (b->dcur0[q] + n - 1) & 1;
+            b->grids[q]->dcur = b->grids[q]->steady ? b->dcur0[q] : (b->dcur0[q] + n - 1) & 1;
+            b->grids[q]->d_cached = 0;
             b->t_host[q] += n * b->dt_host[q];
         }
         b->launches += (unsigned long long)(n + 2);

@@ -25,6 +25,11 @@ struct sl_grid {
     int dcur;                    // index of the current displacement
     int device, num_sms;
     unsigned long long launches;  // kernels launched by this grid's calls (host-side count)
+    // A steady velocity moves every node by the same displacement each step: D(dt) is integrated
+    // once and reused while d_cached says D[dcur] holds it for step d_cached_dt.
+    int steady;
+    int d_cached;
+    double d_cached_dt;
 };
 
 #define SL_MOMENT_BLOCKS 512

@@ -137,6 +137,8 @@ class GpuExecutor:
         self.tile_config = tile_config
         self.lanes: Dict[object, Lane] = {}
         self.launches = 0
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        self.prio_fp64, self.prio_fp32 = lo, hi  # lowest and highest priority the device offers
 
     @staticmethod
     def dtype_code(sl, job):
@@ -166,7 +168,11 @@ class GpuExecutor:
         key = self._lane_key(st)
         lane = self.lanes.get(key)
         if lane is None:
-            lane = self.lanes[key] = Lane(key, torch.cuda.Stream())
+            # FP32 lanes run at high stream priority: when SMs free up the block scheduler serves
+            # them first, so the slow FP64 lanes use the leftover capacity instead of holding the
+            # FP32 work back
+            prio = self.prio_fp64 if code == sl.SL_F64 else self.prio_fp32
+            lane = self.lanes[key] = Lane(key, torch.cuda.Stream(priority=prio))
         g = sl.grid_for(wl, code, tile_config=self.tile_config)
         if isinstance(fields, torch.Tensor):
             f = fields.to(device="cuda", dtype=td).contiguous()

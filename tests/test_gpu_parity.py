@@ -531,3 +531,59 @@ def test_fp32_3d_step_accuracy(sl, orc):
     assert l1 <= 1e-5, l1
     d = g.diagnostics()
     assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
+
+
+def test_full_size_3d_sampled_f32(sl, orc):
+    """256^3 deformation flow (the 3-D benchmark size): the GPU's FP32 remap with the oracle's
+    displacements against the oracle's own element search, order and tricubic sum at sampled targets."""
+    n = 256
+    wl = inputs.workload_deform3d(n, steps=1)
+    og = _og(orc, 3, (n, n, n), 2, velocity="deform3d", params=[3.0])
+    D = orc.advect(og, 0.6, wl.dt)
+    h = wl.fields
+    fl = orc.flags(og, h)
+    g = sl.grid_for(wl, sl.SL_F32)
+    hin = torch.tensor(h, dtype=torch.float32, device=DEV)
+    hout = torch.empty_like(hin)
+    g.set_displacement(torch.tensor(D, dtype=torch.float32, device=DEV))
+    g.remap(hin, hout)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(12)
+    samples = rng.integers(0, n, size=(300, 3))
+    errs = []
+    for (jz, jy, jx) in samples:
+        c, xi, st, _, _ = orc.locate(og, D, (jx, jy, jz))
+        assert st == orc.OK
+        m = orc.order(og, fl, c, 0)
+        v = orc.interp(og, h[0], c, xi, m)
+        errs.append(abs(float(hout[0, jz, jy, jx]) - v))
+    errs = np.array(errs)
+    assert float(np.quantile(errs, 0.99)) <= 1e-5 and float(errs.max()) <= 5e-5, (errs.max(), np.quantile(errs, 0.99))
+    d = g.diagnostics()
+    assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
+
+
+def test_steady_velocity_integrates_once(sl, orc):
+    """For a steady velocity the RK4 displacement over dt is the same every step: sl_step
+    integrates it once and reuses it (also across calls with the same dt); the result equals the
+    oracle's, which integrates every step."""
+    wl = inputs.batched_grids(count=1, seed=2, steps=6, side_lo=96, side_hi=96)[0]
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
+    s = torch.empty_like(f)
+    g.step(f, s, 0.0, wl.dt, 3)
+    l1 = g.diagnostics()["kernel_launches"]
+    g.step(f, s, 3 * wl.dt, wl.dt, 3)
+    assert l1 == 1 + 3 and g.diagnostics()["kernel_launches"] == l1 + 3
+    torch.cuda.synchronize()
+    og = _og(orc, 2, wl.n, 2, velocity=wl.velocity, params=wl.velocity_params)
+    ref, _ = orc.step(og, wl.fields, 0.0, wl.dt, 6)
+    got = f.double().cpu().numpy()
+    assert np.abs(got[0] - ref[0]).sum() / np.abs(ref[0]).sum() <= 1e-4
+    g64 = sl.grid_for(wl, sl.SL_F64)
+    f64 = torch.tensor(wl.fields, device=DEV)
+    g64.step(f64, torch.empty_like(f64), 0.0, wl.dt, 6)
+    torch.cuda.synchronize()
+    assert g64.diagnostics()["kernel_launches"] == 1 + 2 * 6  # one advect, then flags + remap per step
+    err = np.abs(f64.cpu().numpy() - ref)
+    assert float((err > 1e-12 * np.abs(ref).max()).mean()) <= 1e-3
