@@ -121,22 +121,25 @@ class Lane:
         self.stream = stream
         self.members: List[JobState] = []
         self.running: List[JobState] = []
+        self.chunk = 0  # steps of the launch in flight
         self.event = None
         self.batch = None
         self.batch_ids = None
 
 
 class GpuExecutor:
-    """Runs admitted jobs; lanes progress independently (no iteration-wide barrier)."""
+    """Runs admitted jobs; lanes progress independently (no iteration-wide barrier).  A lane
+    advances its jobs by up to `max_chunk` steps per launch (never past a member's last step):
+    fewer host round trips, at the price of a new job waiting up to one chunk to join a batch."""
 
-    def __init__(self, tile_config: int = 0):
+    def __init__(self, tile_config: int = 0, max_chunk: int = 8):
         import torch
 
         from . import sl
         self.torch, self.sl = torch, sl
         self.tile_config = tile_config
+        self.max_chunk = max(1, int(max_chunk))
         self.lanes: Dict[object, Lane] = {}
-        self.launches = 0
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
         self.prio_fp64, self.prio_fp32 = lo, hi  # lowest and highest priority the device offers
 
@@ -190,8 +193,8 @@ class GpuExecutor:
                 continue
             lane.event = None
             for st in lane.running:
-                st.steps_done += 1
-                st.handle["t"] += st.job.workload.dt
+                st.steps_done += lane.chunk
+                st.handle["t"] += lane.chunk * st.job.workload.dt
             lane.running = []
             for st in list(lane.members):
                 if st.steps_done >= st.job.workload.steps:
@@ -211,6 +214,7 @@ class GpuExecutor:
                     lane.batch.close()
                     lane.batch, lane.batch_ids = None, None
                 continue
+            chunk = min([self.max_chunk] + [m.job.workload.steps - m.steps_done for m in lane.members])
             with torch.cuda.stream(lane.stream):
                 if key[0] == "batch":
                     ids = tuple(st.job.job_id for st in lane.members)
@@ -222,13 +226,12 @@ class GpuExecutor:
                                               [m.handle["scratch"] for m in ms], [m.handle["t"] for m in ms],
                                               [m.job.workload.dt for m in ms], tile_config=self.tile_config)
                         lane.batch_ids = ids
-                    lane.batch.step(1, use_graph=False, stream=lane.stream)
-                    self.launches += 4
+                    lane.batch.step(chunk, use_graph=False, stream=lane.stream)
                 else:
                     st = lane.members[0]
                     h = st.handle
-                    h["grid"].step(h["fields"], h["scratch"], h["t"], st.job.workload.dt, 1, stream=lane.stream)
-                    self.launches += 3
+                    h["grid"].step(h["fields"], h["scratch"], h["t"], st.job.workload.dt, chunk, stream=lane.stream)
+                lane.chunk = chunk
                 lane.running = list(lane.members)
                 lane.event = torch.cuda.Event()
                 lane.event.record(lane.stream)
