@@ -92,7 +92,8 @@ typedef struct {
     int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
     int walk_start;                 /* SL_START_BACKWARD (from j - D_j) or SL_START_PAPER (Sec. 2.2) */
     int kernel;                     /* SL_KERNEL_AUTO, SL_KERNEL_GENERIC or SL_KERNEL_TILED           */
-    int tile_config;                /* 2-D FP32 tiles: 0 default (= 1), 1: 32x32, 2: 32x16, 3: 64x16  */
+    int tile_config;                /* 2-D FP32 tiles: 0 default (= 1), 1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16
+                                       compiled for 4 CTAs per SM                                 */
 } sl_grid_desc;
 
 /* Counters accumulated on the device since creation or the last sl_reset_diagnostics. */
@@ -180,7 +181,7 @@ sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], co
  * aligned); the library allocates no device memory. */
 typedef struct sl_batch sl_batch;
 
-/* Workspace bytes of a batch of these grids with tile configuration tile_config (0..3, as in
+/* Workspace bytes of a batch of these grids with tile configuration tile_config (0..4, as in
  * sl_grid_desc); 0 if a grid is not eligible. */
 size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config);
 

@@ -52,7 +52,7 @@ static const char *check_desc(const sl_grid_desc *d)
     if (d->fail_policy != SL_FAIL_KEEP && d->fail_policy != SL_FAIL_ERROR) return "bad fail_policy";
     if (d->walk_start != SL_START_BACKWARD && d->walk_start != SL_START_PAPER) return "bad walk_start";
     if (d->kernel < SL_KERNEL_AUTO || d->kernel > SL_KERNEL_TILED) return "bad kernel";
-    if (d->tile_config < 0 || d->tile_config > 3) return "tile_config must be in [0, 3]";
+    if (d->tile_config < 0 || d->tile_config > 4) return "tile_config must be in [0, 4]";
     if (d->newton_max_iter > 64 || d->walk_max > 4096) return "newton_max_iter <= 64 and walk_max <= 4096";
     const int np = d->n_velocity_params;
     if (np < 0 || np > SL_MAX_VEL_PARAMS) return "n_velocity_params out of range";

@@ -64,7 +64,7 @@ __device__ __forceinline__ int next_item(unsigned *counter, int *s_item)
 }
 
 template <class Cfg, int NF>
-__global__ void __launch_bounds__(Cfg::NT, 3)
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
     batch_step_kernel(const BatchGrid *__restrict__ table, const int *__restrict__ item_grid, int nitems,
                       unsigned *counter, const double *__restrict__ tgrid, int k, int last)
 {
@@ -185,7 +185,7 @@ void tiles_of(const sl_grid *g, int *tx, int *ty)
 
 void tile_counts(int cfg, const sl_grid *g, int *tx, int *ty)
 {
-    if (cfg == 2)
+    if (cfg == 2 || cfg == 4)
         tiles_of<CfgB>(g, tx, ty);
     else if (cfg == 3)
         tiles_of<CfgC>(g, tx, ty);
@@ -220,7 +220,7 @@ static bool batch_eligible(const sl_grid *g)
 
 extern "C" size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config)
 {
-    if (!grids || count < 1 || tile_config < 0 || tile_config > 3) return 0;
+    if (!grids || count < 1 || tile_config < 0 || tile_config > 4) return 0;
     long long nitems = 0;
     for (int q = 0; q < count; ++q) {
         if (!batch_eligible(grids[q])) return 0;
@@ -239,7 +239,7 @@ extern "C" sl_status sl_batch_create(sl_grid *const *grids, int count, void *con
     if (!out) return SL_ERR_ARG;
     *out = nullptr;
     if (!grids || count < 1 || !fields || !scratch || !t0 || !dt || !dev_workspace) return SL_ERR_ARG;
-    if (tile_config < 0 || tile_config > 3) return SL_ERR_ARG;
+    if (tile_config < 0 || tile_config > 4) return SL_ERR_ARG;
     if (((uintptr_t)dev_workspace & 255u) != 0) return SL_ERR_ARG;
     const int nf = grids[0] ? grids[0]->nfields : 0;
     if (nf < 1 || nf > 4) return SL_ERR_UNSUPPORTED;
@@ -344,6 +344,7 @@ static cudaError_t launch_batch_cfg(sl_batch *b, int nsteps, cudaStream_t s)
 static cudaError_t launch_batch(sl_batch *b, int nsteps, cudaStream_t s)
 {
     if (b->cfg == 2) return launch_batch_cfg<CfgB>(b, nsteps, s);
+    if (b->cfg == 4) return launch_batch_cfg<CfgD>(b, nsteps, s);
     if (b->cfg == 3) return launch_batch_cfg<CfgC>(b, nsteps, s);
     return launch_batch_cfg<CfgA>(b, nsteps, s);
 }

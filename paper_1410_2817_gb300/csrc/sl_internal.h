@@ -58,7 +58,8 @@ cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, cons
                              double dt, bool fused, const void *const *in, void *const *out, cudaStream_t s);
 // kernels one tiled remap / fused step call launches
 int tiled_kernels_per_call(const sl_grid *g);
-// 2-D FP32 tiled kernels per tile configuration (sl_tiled_cfg_*.cu): a 32x32, b 32x16, c 64x16
+// 2-D FP32 tiled kernels per tile configuration (sl_tiled_cfg_*.cu): a 32x32, b 32x16, c 64x16,
+// d 32x16 at 4 CTAs per SM
 cudaError_t launch_tiled2d_cfga(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                                 const void *const *in, void *const *out, cudaStream_t s);
 cudaError_t launch_tiled2d_cfgb(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
@@ -68,6 +69,9 @@ cudaError_t launch_tiled2d_cfgc(const sl_grid *g, const void *D, void *D_next, d
 size_t tiled2d_smem_bytes_cfga(int nfields);
 size_t tiled2d_smem_bytes_cfgb(int nfields);
 size_t tiled2d_smem_bytes_cfgc(int nfields);
+cudaError_t launch_tiled2d_cfgd(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
+                                const void *const *in, void *const *out, cudaStream_t s);
+size_t tiled2d_smem_bytes_cfgd(int nfields);
 
 // shared argument builders (sl_kernels.cu)
 template <typename T>

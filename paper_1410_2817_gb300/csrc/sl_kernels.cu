@@ -67,11 +67,14 @@ VelArgs<T> make_vel_args(const sl_grid *g, double t, double dt)
     return v;
 }
 
+// One block per `threads` nodes (the kernels also loop grid-stride, so any count is correct).
+// Short-lived blocks let the block scheduler interleave work of higher-priority streams; the cap
+// only guards the grid-size limit.
 int grid_stride_blocks(const sl_grid *g, long long work, int threads)
 {
+    (void)g;
     long long b = (work + threads - 1) / threads;
-    long long cap = (long long)g->num_sms * 16;
-    if (b > cap) b = cap;
+    if (b > (1LL << 30)) b = 1LL << 30;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -28,9 +28,10 @@ namespace {
 
 // Tile configuration: TX x TY targets per CTA of NT threads (TX a multiple of 32: one warp per
 // row segment), window capacity (TX + 2 HALO) x (TY + 2 HALO) nodes in shared memory.
-template <int TX_, int TY_, int NT_, int HALO_>
+template <int TX_, int TY_, int NT_, int HALO_, int MINB_ = 3>
 struct TileCfg {
     static constexpr int TX = TX_, TY = TY_, NT = NT_, HALO = HALO_;
+    static constexpr int MINB = MINB_;     // CTAs per SM the register budget is compiled for
     static constexpr int ROWS = NT / TX;   // thread rows
     static constexpr int TPT = TY / ROWS;  // targets per thread
     static constexpr int WMAX = (TX + 2 * HALO) * (TY + 2 * HALO);
@@ -39,6 +40,7 @@ struct TileCfg {
 typedef TileCfg<32, 32, 256, 8> CfgA;  // default
 typedef TileCfg<32, 16, 256, 8> CfgB;
 typedef TileCfg<64, 16, 256, 8> CfgC;
+typedef TileCfg<32, 16, 256, 8, 4> CfgD;  // 4 CTAs per SM: at most 64 registers per thread
 
 constexpr int WALK_SLACK = 1;          // elements the walk may step beyond the start-cell box
 
@@ -491,7 +493,7 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
 }
 
 template <class Cfg, int NF, bool FUSED>
-__global__ void __launch_bounds__(Cfg::NT, 3) remap_tiled2d_kernel(const TileArgs a, const VelArgs<float> vn)
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const TileArgs a, const VelArgs<float> vn)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sBox[4];

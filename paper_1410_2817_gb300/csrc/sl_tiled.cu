@@ -14,8 +14,10 @@ bool Launch<T>::tiled_supported(const sl_grid *g)
     if (sizeof(T) != 4 || g->desc.max_order > 1 || g->desc.walk_start != SL_START_BACKWARD) return false;
     if (g->dim == 3) return true;
     const int c = g->desc.tile_config;
-    const size_t smem = c == 2 ? tiled2d_smem_bytes_cfgb(g->nfields)
-                        : c == 3 ? tiled2d_smem_bytes_cfgc(g->nfields) : tiled2d_smem_bytes_cfga(g->nfields);
+    const size_t smem = c == 2   ? tiled2d_smem_bytes_cfgb(g->nfields)
+                        : c == 3 ? tiled2d_smem_bytes_cfgc(g->nfields)
+                        : c == 4 ? tiled2d_smem_bytes_cfgd(g->nfields)
+                                 : tiled2d_smem_bytes_cfga(g->nfields);
     return smem <= 200 * 1024;
 }
 
@@ -25,6 +27,7 @@ static cudaError_t launch_tiled2d(const sl_grid *g, const void *D, void *D_next,
     switch (g->desc.tile_config) {
     case 2: return launch_tiled2d_cfgb(g, D, D_next, t_next, dt, fused, in, out, s);
     case 3: return launch_tiled2d_cfgc(g, D, D_next, t_next, dt, fused, in, out, s);
+    case 4: return launch_tiled2d_cfgd(g, D, D_next, t_next, dt, fused, in, out, s);
     default: return launch_tiled2d_cfga(g, D, D_next, t_next, dt, fused, in, out, s);
     }
 }
