@@ -23,11 +23,7 @@ struct Geo3 {
     int n0, n1, n2;
 };
 
-__device__ __forceinline__ int wrap3(int k, int n)
-{
-    int r = k % n;
-    return r < 0 ? r + n : r;
-}
+__device__ __forceinline__ int wrap3(int k, int n) { return wrap_idx(k, n); }
 
 __device__ __forceinline__ long long lin3(const Geo3 &g, int x, int y, int z)
 {
@@ -95,15 +91,32 @@ __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D
 {
     const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(SL_NEWTON_TOL_F32);
     const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(SL_SLACK_F32);
+    const long long sy = g.n0, sz = (long long)g.n0 * g.n1;
     for (int hop = 0; hop < walk_max; ++hop) {
         TN P[8][3];
+        float4 d8[8];
+        // c[a] in [0, n[a] - 2] on every axis (a negative c fails the unsigned compare)
+        if ((unsigned)c[0] < (unsigned)(g.n0 - 1) && (unsigned)c[1] < (unsigned)(g.n1 - 1) &&
+            (unsigned)c[2] < (unsigned)(g.n2 - 1)) {
+            // the element does not touch the periodic seam: vertices at fixed offsets
+            const float4 *b = D + ((long long)c[2] * g.n1 + c[1]) * g.n0 + c[0];
+            d8[0] = __ldg(b);
+            d8[1] = __ldg(b + 1);
+            d8[2] = __ldg(b + sy);
+            d8[3] = __ldg(b + sy + 1);
+            d8[4] = __ldg(b + sz);
+            d8[5] = __ldg(b + sz + 1);
+            d8[6] = __ldg(b + sz + sy);
+            d8[7] = __ldg(b + sz + sy + 1);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) d8[v] = __ldg(D + lin3(g, c[0] + (v & 1), c[1] + ((v >> 1) & 1), c[2] + (v >> 2)));
+        }
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            const int kx = c[0] + (v & 1), ky = c[1] + ((v >> 1) & 1), kz = c[2] + (v >> 2);
-            const float4 d = __ldg(D + lin3(g, kx, ky, kz));
-            P[v][0] = TN(kx - j[0]) + TN(d.x);
-            P[v][1] = TN(ky - j[1]) + TN(d.y);
-            P[v][2] = TN(kz - j[2]) + TN(d.z);
+            P[v][0] = TN(c[0] + (v & 1) - j[0]) + TN(d8[v].x);
+            P[v][1] = TN(c[1] + ((v >> 1) & 1) - j[1]) + TN(d8[v].y);
+            P[v][2] = TN(c[2] + (v >> 2) - j[2]) + TN(d8[v].z);
         }
         int it = 0;
         const int st = newton_solve3<TN>(P, max_iter, tol, xi, &it, degen);
@@ -128,6 +141,21 @@ __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D
     return ST_LOCATE;
 }
 
+// FP64 re-solve of a target whose FP32 inversion failed or whose element is nearly degenerate
+// (rare: out of line so that it costs the main path no registers)
+__device__ __noinline__ int resolve3_f64(const Geo3 &g, const float4 *__restrict__ D, int max_iter, int walk_max,
+                                         const int j[3], const int c0[3], int st32, int c[3], float xf[3], int &hops,
+                                         int &iters)
+{
+    double xd[3] = {0.0, 0.0, 0.0};
+    bool degd = false;
+    if (st32 == ST_LOCATE || st32 == ST_FOLD)
+        for (int q = 0; q < 3; ++q) c[q] = c0[q];
+    const int st = walk3<double>(g, D, max_iter, walk_max, j, c, xd, hops, iters, &degd);
+    for (int q = 0; q < 3; ++q) xf[q] = (float)xd[q];
+    return st;
+}
+
 struct Blocked3Args {
     Geo3 g;
     int nfields, max_order, max_iter, walk_max;
@@ -138,8 +166,57 @@ struct Blocked3Args {
     DevCounters *counters;
 };
 
-template <bool FUSED>
-__global__ void __launch_bounds__(NT3, 2) remap_blocked3d_kernel(const Blocked3Args a, const VelArgs<float> vn)
+// eq. (multiZ) in 3-D for up to NFM fields: the 4x4x4 cubic (Z~1) sums and the trilinear (Z~0)
+// sums over the element's 8 vertices in one pass.  Row offsets are shared by all fields; with
+// XIN (the stencil does not cross the x seam) the 4 taps of a row sit at x0 .. x0+3.
+template <int NFM, bool XIN>
+__device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4], const long long oy[4],
+                                         const long long oz[4], int x0, const float wc[3][4], const float xf[3],
+                                         float cub[NFM], float lin[NFM])
+{
+#pragma unroll
+    for (int q = 0; q < NFM; ++q) cub[q] = lin[q] = 0.f;
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+        float syc[NFM], syl[NFM];
+#pragma unroll
+        for (int q = 0; q < NFM; ++q) syc[q] = syl[q] = 0.f;
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+            const long long ro = oz[kz] + oy[ky];
+#pragma unroll
+            for (int q = 0; q < NFM; ++q) {
+                if (q >= a.nfields) break;
+                const float *row = a.f.in[q] + ro;
+                float t0, t1, t2, t3;
+                if (XIN) {
+                    row += x0;
+                    t0 = __ldg(row);
+                    t1 = __ldg(row + 1);
+                    t2 = __ldg(row + 2);
+                    t3 = __ldg(row + 3);
+                } else {
+                    t0 = __ldg(row + ox[0]);
+                    t1 = __ldg(row + ox[1]);
+                    t2 = __ldg(row + ox[2]);
+                    t3 = __ldg(row + ox[3]);
+                }
+                const float r = fmaf(wc[0][3], t3, fmaf(wc[0][2], t2, fmaf(wc[0][1], t1, wc[0][0] * t0)));
+                syc[q] = fmaf(wc[1][ky], r, syc[q]);
+                if (ky == 1 || ky == 2)
+                    syl[q] = fmaf(ky == 1 ? 1.f - xf[1] : xf[1], fmaf(xf[0], t2, (1.f - xf[0]) * t1), syl[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NFM; ++q) {
+            cub[q] = fmaf(wc[2][kz], syc[q], cub[q]);
+            if (kz == 1 || kz == 2) lin[q] = fmaf(kz == 1 ? 1.f - xf[2] : xf[2], syl[q], lin[q]);
+        }
+    }
+}
+
+template <int NFM, bool FUSED>
+__global__ void __launch_bounds__(NT3, 3) remap_blocked3d_kernel(const Blocked3Args a, const VelArgs<float> vn)
 {
     const Geo3 &g = a.g;
     const int jx = blockIdx.x * BX + threadIdx.x % BX;
@@ -153,22 +230,38 @@ __global__ void __launch_bounds__(NT3, 2) remap_blocked3d_kernel(const Blocked3A
         const float4 dj = __ldg(a.D + jj);
         const float djv[3] = {dj.x, dj.y, dj.z};
         int c[3], c0[3];
+        float s0[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const float s = fminf(fmaxf((float)j[q] - djv[q], (float)j[q] - 65536.f), (float)j[q] + 65536.f);
-            c0[q] = c[q] = finite_t(s) ? (int)floorf(s) : j[q];
+            s0[q] = finite_t(s) ? s : (float)j[q];
+            c0[q] = c[q] = (int)floorf(s0[q]);
+        }
+        {
+            // start element: one fixed-point step s <- j - D(s) from s0 = j - D_j, with D(s0)
+            // trilinear over the 8 nodes around s0 (the walk below still decides)
+            const float fx = s0[0] - (float)c0[0], fy = s0[1] - (float)c0[1], fz = s0[2] - (float)c0[2];
+            float dd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const float4 d = __ldg(a.D + lin3(g, c0[0] + (v & 1), c0[1] + ((v >> 1) & 1), c0[2] + (v >> 2)));
+                const float w = ((v & 1) ? fx : 1.f - fx) * (((v >> 1) & 1) ? fy : 1.f - fy) * ((v >> 2) ? fz : 1.f - fz);
+                dd[0] = fmaf(w, d.x, dd[0]);
+                dd[1] = fmaf(w, d.y, dd[1]);
+                dd[2] = fmaf(w, d.z, dd[2]);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float r = (float)j[q] - dd[q];
+                if (finite_t(r) && fabsf(r - s0[q]) < 4.f) c[q] = (int)floorf(r);
+            }
         }
         int hops = 0, iters = 0;
         float xf[3] = {0.f, 0.f, 0.f};
         bool degen = false;
         int st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters, &degen);
         if (st != ST_OK || degen) {
-            double xd[3] = {0.0, 0.0, 0.0};
-            bool degd = false;
-            if (st == ST_LOCATE || st == ST_FOLD)
-                for (int q = 0; q < 3; ++q) c[q] = c0[q];
-            st = walk3<double>(g, a.D, a.max_iter, a.walk_max, j, c, xd, hops, iters, &degd);
-            for (int q = 0; q < 3; ++q) xf[q] = (float)xd[q];
+            st = resolve3_f64(g, a.D, a.max_iter, a.walk_max, j, c0, st, c, xf, hops, iters);
             cnt.f64 += 1;
         }
         cnt.targets = 1;
@@ -195,41 +288,18 @@ __global__ void __launch_bounds__(NT3, 2) remap_blocked3d_kernel(const Blocked3A
                 oy[k] = (long long)wrap3(c[1] - 1 + k, g.n1) * g.n0;
                 oz[k] = (long long)wrap3(c[2] - 1 + k, g.n2) * g.n0 * g.n1;
             }
-            for (int q = 0; q < a.nfields; ++q) {
-                const float *h = a.f.in[q];
-                const bool lin = ((bits >> q) & 1u) != 0u;
-                cnt.oh0 += lin;
-                cnt.oh1 += !lin;
-                float sum = 0.f;
-                if (lin) {
-                    // Z~0: trilinear over the element's 8 vertices (taps 1, 2 of each axis)
-                    for (int kz = 1; kz <= 2; ++kz) {
-                        const float wz = kz == 1 ? 1.f - xf[2] : xf[2];
-                        float sy = 0.f;
-                        for (int ky = 1; ky <= 2; ++ky) {
-                            const float wy = ky == 1 ? 1.f - xf[1] : xf[1];
-                            const float *row = h + oz[kz] + oy[ky];
-                            const float r = fmaf(xf[0], __ldg(row + ox[2]), (1.f - xf[0]) * __ldg(row + ox[1]));
-                            sy = fmaf(wy, r, sy);
-                        }
-                        sum = fmaf(wz, sy, sum);
-                    }
-                } else {
+            float cub[NFM], lin[NFM];
+            if (c[0] >= 1 && c[0] + 2 < g.n0)
+                tap_sums<NFM, true>(a, ox, oy, oz, c[0] - 1, wc, xf, cub, lin);
+            else
+                tap_sums<NFM, false>(a, ox, oy, oz, 0, wc, xf, cub, lin);
 #pragma unroll
-                    for (int kz = 0; kz < 4; ++kz) {
-                        float sy = 0.f;
-#pragma unroll
-                        for (int ky = 0; ky < 4; ++ky) {
-                            const float *row = h + oz[kz] + oy[ky];
-                            const float r = fmaf(wc[0][3], __ldg(row + ox[3]),
-                                                 fmaf(wc[0][2], __ldg(row + ox[2]),
-                                                      fmaf(wc[0][1], __ldg(row + ox[1]), wc[0][0] * __ldg(row + ox[0]))));
-                            sy = fmaf(wc[1][ky], r, sy);
-                        }
-                        sum = fmaf(wc[2][kz], sy, sum);
-                    }
-                }
-                a.f.out[q][jj] = sum;
+            for (int q = 0; q < NFM; ++q) {
+                if (q >= a.nfields) break;
+                const bool useL = ((bits >> q) & 1u) != 0u;
+                cnt.oh0 += useL;
+                cnt.oh1 += !useL;
+                a.f.out[q][jj] = useL ? lin[q] : cub[q];
             }
         }
         if (FUSED && a.D_next != nullptr) {
@@ -280,13 +350,18 @@ cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, cons
     a.counters = g->counters;
     dim3 grid((unsigned)((g->n[0] + BX - 1) / BX), (unsigned)((g->n[1] + BY - 1) / BY),
               (unsigned)((g->n[2] + BZ - 1) / BZ));
+    VelArgs<float> vn;
+    memset(&vn, 0, sizeof(vn));
+    if (fused) vn = make_vel_args<float>(g, t_next, dt);
+    const int nfm = g->nfields <= 2 ? 2 : g->nfields <= 4 ? 4 : 8;
     if (fused) {
-        const VelArgs<float> vn = make_vel_args<float>(g, t_next, dt);
-        remap_blocked3d_kernel<true><<<grid, NT3, 0, s>>>(a, vn);
+        if (nfm == 2) remap_blocked3d_kernel<2, true><<<grid, NT3, 0, s>>>(a, vn);
+        else if (nfm == 4) remap_blocked3d_kernel<4, true><<<grid, NT3, 0, s>>>(a, vn);
+        else remap_blocked3d_kernel<8, true><<<grid, NT3, 0, s>>>(a, vn);
     } else {
-        VelArgs<float> vn;
-        memset(&vn, 0, sizeof(vn));
-        remap_blocked3d_kernel<false><<<grid, NT3, 0, s>>>(a, vn);
+        if (nfm == 2) remap_blocked3d_kernel<2, false><<<grid, NT3, 0, s>>>(a, vn);
+        else if (nfm == 4) remap_blocked3d_kernel<4, false><<<grid, NT3, 0, s>>>(a, vn);
+        else remap_blocked3d_kernel<8, false><<<grid, NT3, 0, s>>>(a, vn);
     }
     return cudaGetLastError();
 }

@@ -55,8 +55,10 @@ enum { ST_OK = 0, ST_LOCATE = 1, ST_NEWTON = 2, ST_FOLD = 3 };
 // ------------------------------------------------------------------------------------------------
 // small helpers
 // ------------------------------------------------------------------------------------------------
+// periodic index: a compare and select for the common case, a modulo only for k outside [0, n)
 __device__ __forceinline__ int wrap_idx(int k, int n)
 {
+    if ((unsigned)k < (unsigned)n) return k;
     int r = k % n;
     return r < 0 ? r + n : r;
 }
@@ -274,9 +276,10 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
         return ST_FOLD;
     }
     T r0 = -P0[0], r1 = -P0[1], r2 = -P0[2];
-    T s0 = det3(r0, A[0][1], A[0][2], r1, A[1][1], A[1][2], r2, A[2][1], A[2][2]) / det;
-    T s1 = det3(A[0][0], r0, A[0][2], A[1][0], r1, A[1][2], A[2][0], r2, A[2][2]) / det;
-    T s2 = det3(A[0][0], A[0][1], r0, A[1][0], A[1][1], r1, A[2][0], A[2][1], r2) / det;
+    T inv = recip_t(det);
+    T s0 = det3(r0, A[0][1], A[0][2], r1, A[1][1], A[1][2], r2, A[2][1], A[2][2]) * inv;
+    T s1 = det3(A[0][0], r0, A[0][2], A[1][0], r1, A[1][2], A[2][0], r2, A[2][2]) * inv;
+    T s2 = det3(A[0][0], A[0][1], r0, A[1][0], A[1][1], r1, A[2][0], A[2][1], r2) * inv;
     for (int it = 1; it <= max_iter; ++it) {
         *iters = it;
         T F[3], J[3][3];
@@ -295,9 +298,10 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
             xi[2] = s2;
             return ST_FOLD;
         }
-        const T d0 = det3(F[0], J[0][1], J[0][2], F[1], J[1][1], J[1][2], F[2], J[2][1], J[2][2]) / det;
-        const T d1 = det3(J[0][0], F[0], J[0][2], J[1][0], F[1], J[1][2], J[2][0], F[2], J[2][2]) / det;
-        const T d2 = det3(J[0][0], J[0][1], F[0], J[1][0], J[1][1], F[1], J[2][0], J[2][1], F[2]) / det;
+        inv = recip_t(det);
+        const T d0 = det3(F[0], J[0][1], J[0][2], F[1], J[1][1], J[1][2], F[2], J[2][1], J[2][2]) * inv;
+        const T d1 = det3(J[0][0], F[0], J[0][2], J[1][0], F[1], J[1][2], J[2][0], F[2], J[2][2]) * inv;
+        const T d2 = det3(J[0][0], J[0][1], F[0], J[1][0], J[1][1], F[1], J[2][0], J[2][1], F[2]) * inv;
         s0 -= d0;
         s1 -= d1;
         s2 -= d2;
