@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
     __shared__ __align__(16) BatchGrid sg;
     __shared__ TileArgs sa;
     __shared__ VelArgs<float> sv;
-    const TileSmem<NF, Cfg::WMAX> sm(smem);
+    const TileSmem<Cfg, NF> sm(smem);
     for (int item = next_item(counter, &s_item); item < nitems; item = next_item(counter, &s_item)) {
         const int gid = __ldg(item_grid + item);
         load_entry(table, gid, &sg);

@@ -63,6 +63,12 @@ __device__ __forceinline__ int wrap_idx(int k, int n)
     return r < 0 ? r + n : r;
 }
 
+// periodic index for k in [-n, 2n) only (callers guarantee the range): compares and one add
+__device__ __forceinline__ int wrap_near(int k, int n)
+{
+    return k < 0 ? k + n : (k >= n ? k - n : k);
+}
+
 // Type-exact math: a float argument must never reach a double overload (GB300 runs FP64 at a
 // small fraction of its FP32 rate, so one stray conversion per tap or iteration dominates).
 __device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
@@ -77,7 +83,14 @@ __device__ __forceinline__ bool finite_t(double x) { return fabs(x) <= 1.7976931
 
 // 1/x: the FP32 paths take the approximate hardware reciprocal (Newton converges to the root of
 // x(xi) = 0 whatever the last bits of J^-1 are), FP64 keeps the IEEE division
-__device__ __forceinline__ float recip_t(float x) { return __fdividef(1.0f, x); }
+// FP32: the hardware's approximate reciprocal (within a few ulp; denormals flush to zero).  The
+// Newton step tolerance is far above its error, and a determinant that small is degenerate anyway.
+__device__ __forceinline__ float recip_t(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double recip_t(double x) { return 1.0 / x; }
 
 __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }

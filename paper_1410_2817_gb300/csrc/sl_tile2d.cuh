@@ -56,25 +56,9 @@ struct TileArgs {
     DevCounters *counters;
 };
 
-__device__ __forceinline__ int wrapi(int k, int n)
-{
-    int r = k % n;
-    return r < 0 ? r + n : r;
-}
-
-// wrap with a modulo only when k is outside [0, n)
-__device__ __forceinline__ int wrap_fast(int k, int n) { return (unsigned)k < (unsigned)n ? k : wrapi(k, n); }
-
-// start element floor(j - D_j), clamped so that garbage displacements cannot overflow the walk
-__device__ __forceinline__ int start_cell(int j, float d)
-{
-    const float s = fminf(fmaxf((float)j - d, (float)j - 65536.f), (float)j + 65536.f);
-    return finite_t(s) ? (int)floorf(s) : j;
-}
-
 __device__ __forceinline__ long long gidx(int x, int y, int n0, int n1)
 {
-    return (long long)wrap_fast(y, n1) * n0 + wrap_fast(x, n0);
+    return (long long)wrap_idx(y, n1) * n0 + wrap_idx(x, n0);
 }
 
 // asynchronous global -> shared copies (LDGSTS); a CTA issues its whole window, then waits once
@@ -152,22 +136,48 @@ __device__ __forceinline__ int walk2(const TileArgs &a, const Win &w, const floa
     return ST_LOCATE;
 }
 
-// FP64 re-solve of a target whose FP32 inversion failed or whose element is nearly degenerate
-// (rare: kept out of line so that it costs the main path no registers)
-__device__ __noinline__ int resolve_f64(const TileArgs &a, const Win &w, const float2 *sD, int jx, int jy, int st32,
-                                        int c0x, int c0y, int &ex, int &ey, float &xi0, float &xi1, int &hops,
-                                        int &iters)
+// Sec. 2.2 element search entirely in the staged window, FP32 Newton.  Returns false when an
+// element leaves the window, Newton does not converge or the element is nearly degenerate: the
+// target is then solved again on the general path (slow_target), which repeats this walk with
+// global reads and re-solves in FP64.  The arithmetic is that of walk2<float>, so a target that
+// succeeds here gets the same element and coordinates as on the general path.
+__device__ __forceinline__ bool walk_window(const Win &w, const float2 *sD, int walk_max, int max_iter, int jx, int jy,
+                                            int &ex, int &ey, float &xi0, float &xi1, int &hops, int &iters)
 {
-    if (st32 == ST_LOCATE || st32 == ST_FOLD) {
-        ex = c0x;
-        ey = c0y;
+    const float slack = SL_SLACK_F32;
+    for (int hop = 0; hop < walk_max; ++hop) {
+        if (!(w.has(ex, ey) && w.has(ex + 1, ey + 1))) return false;
+        const int i0 = w.at(ex, ey);
+        const float2 d0 = sD[i0], d1 = sD[i0 + 1], d2 = sD[i0 + w.wx], d3 = sD[i0 + w.wx + 1];
+        const float rx0 = (float)(ex - jx), rx1 = (float)(ex + 1 - jx);
+        const float ry0 = (float)(ey - jy), ry1 = (float)(ey + 1 - jy);
+        float P[8][3];
+        P[0][0] = rx0 + d0.x;
+        P[0][1] = ry0 + d0.y;
+        P[1][0] = rx1 + d1.x;
+        P[1][1] = ry0 + d1.y;
+        P[2][0] = rx0 + d2.x;
+        P[2][1] = ry1 + d2.y;
+        P[3][0] = rx1 + d3.x;
+        P[3][1] = ry1 + d3.y;
+        float xf[3];
+        int it = 0;
+        bool degen = false;
+        const int st = newton_solve2<float>(P, max_iter, SL_NEWTON_TOL_F32, xf, &it, &degen);
+        hops += 1;
+        iters += it;
+        if (st != ST_OK || degen) return false;  // converged implies finite coordinates
+        const bool lo0 = xf[0] < -slack, hi0 = xf[0] > 1.f + slack;
+        const bool lo1 = xf[1] < -slack, hi1 = xf[1] > 1.f + slack;
+        if (!(lo0 || hi0 || lo1 || hi1)) {
+            xi0 = xf[0];
+            xi1 = xf[1];
+            return true;
+        }
+        ex += lo0 ? -1 : (hi0 ? 1 : 0);
+        ey += lo1 ? -1 : (hi1 ? 1 : 0);
     }
-    double xd[3] = {0.0, 0.0, 0.0};
-    bool degen = false;
-    const int st = walk2<double>(a, w, sD, jx, jy, ex, ey, xd, hops, iters, degen);
-    xi0 = (float)xd[0];
-    xi1 = (float)xd[1];
-    return st;
+    return false;
 }
 
 // Sec. 2.3 flags of one node from global memory (fallback path)
@@ -229,22 +239,6 @@ __device__ __noinline__ void interp_global(const TileArgs &a, long long jj, int 
     }
 }
 
-// w * v + acc on the first NC components (the others are left as they are)
-template <int NC>
-__device__ __forceinline__ float4 fma4(float w, const float4 &v, const float4 &acc)
-{
-    return make_float4(fmaf(w, v.x, acc.x), NC > 1 ? fmaf(w, v.y, acc.y) : acc.y, NC > 2 ? fmaf(w, v.z, acc.z) : acc.z,
-                       NC > 3 ? fmaf(w, v.w, acc.w) : acc.w);
-}
-
-template <int NC>
-__device__ __forceinline__ float4 mul4(float w, const float4 &v)
-{
-    return make_float4(w * v.x, NC > 1 ? w * v.y : 0.f, NC > 2 ? w * v.z : 0.f, NC > 3 ? w * v.w : 0.f);
-}
-
-__device__ __forceinline__ float comp(const float4 &v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
-
 // jump bits (Sec. 2.3) of the first NC fields interleaved in a float4
 template <int NC>
 __device__ __forceinline__ unsigned jump4(const float4 &m, const float4 &c, const float4 &p, float thr)
@@ -262,52 +256,171 @@ __host__ __device__ constexpr int in_group(int nf, int g) { return nf - 4 * g < 
 
 // eq. (multiZ) for the fields of group G (4 per float4) from the 4x4 taps starting at h: the cubic
 // (Z~1) sum and the bilinear (Z~0) sum over the element's own 4 vertices; fields whose lin_mask bit
-// is set take the bilinear value.
+// is set take the bilinear value.  The sums run on field pairs with packed FP32x2 FMAs (each lane
+// rounds as fmaf does); the pair holding only padding is skipped.
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
 template <int NF, int G>
 __device__ __forceinline__ void store_group(const TileArgs &a, long long jj, const float4 *h, int stride,
                                             const float wc[2][4], float xi0, float xi1, unsigned lin_mask)
 {
     constexpr int NC = in_group(NF, G);
-    float4 cub = make_float4(0.f, 0.f, 0.f, 0.f), lin = cub;
+    constexpr bool HI = NC > 2;
+    const float2 w0 = bcast2(wc[0][0]), w1 = bcast2(wc[0][1]), w2 = bcast2(wc[0][2]), w3 = bcast2(wc[0][3]);
+    const float2 u0 = bcast2(1.f - xi0), u1 = bcast2(xi0);
+    const float2 z = make_float2(0.f, 0.f);
+    float2 cl = z, ch = z, ll = z, lh = z;
 #pragma unroll
     for (int ky = 0; ky < 4; ++ky) {
         const float4 t0 = h[0], t1 = h[1], t2 = h[2], t3 = h[3];
-        float4 r = mul4<NC>(wc[0][0], t0);
-        r = fma4<NC>(wc[0][1], t1, r);
-        r = fma4<NC>(wc[0][2], t2, r);
-        r = fma4<NC>(wc[0][3], t3, r);
-        cub = fma4<NC>(wc[1][ky], r, cub);
-        if (ky == 1 || ky == 2) lin = fma4<NC>(ky == 1 ? 1.f - xi1 : xi1, fma4<NC>(xi0, t2, mul4<NC>(1.f - xi0, t1)), lin);
+        const float2 wy = bcast2(wc[1][ky]);
+        float2 r = __fmul2_rn(w0, lo2(t0));
+        r = __ffma2_rn(w1, lo2(t1), r);
+        r = __ffma2_rn(w2, lo2(t2), r);
+        r = __ffma2_rn(w3, lo2(t3), r);
+        cl = __ffma2_rn(wy, r, cl);
+        if (HI) {
+            float2 q = __fmul2_rn(w0, hi2(t0));
+            q = __ffma2_rn(w1, hi2(t1), q);
+            q = __ffma2_rn(w2, hi2(t2), q);
+            q = __ffma2_rn(w3, hi2(t3), q);
+            ch = __ffma2_rn(wy, q, ch);
+        }
+        if (ky == 1 || ky == 2) {
+            const float2 v = bcast2(ky == 1 ? 1.f - xi1 : xi1);
+            ll = __ffma2_rn(v, __ffma2_rn(u1, lo2(t2), __fmul2_rn(u0, lo2(t1))), ll);
+            if (HI) lh = __ffma2_rn(v, __ffma2_rn(u1, hi2(t2), __fmul2_rn(u0, hi2(t1))), lh);
+        }
         h += stride;
     }
+    const float cub[4] = {cl.x, cl.y, ch.x, ch.y}, lin[4] = {ll.x, ll.y, lh.x, lh.y};
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int f = 4 * G + c;
-        a.out[f][jj] = ((lin_mask >> f) & 1u) ? comp(lin, c) : comp(cub, c);
+        a.out[f][jj] = ((lin_mask >> f) & 1u) ? lin[c] : cub[c];
     }
 }
 
-// Shared memory of one tile: displacements, fields (4 per float4), flags, row-OR, box-OR.
-template <int NF, int WMAX>
+// Words of one field's bit plane: rows x ceil(wx / 32) <= (WMAX + 31 WMAX / 8) / 32, because every
+// staged window is at least 8 nodes wide and high.
+__host__ __device__ constexpr int mask_words(int wmax) { return (wmax + 31 * (wmax / 8)) / 32 + 1; }
+
+// Shared memory of one tile: displacements, fields (4 per float4), per field two bit planes of
+// ceil(wx / 32) words per window row -- M, the jump flags of the interior nodes, and B, bit x of row
+// y set when a flag lies among nodes x-1 .. x+2 of rows y-1 .. y+2 (element (x, y)'s stencil) --
+// and the start points j - D_j of the tile's targets.
+template <class Cfg, int NF>
 struct TileSmem {
+    static constexpr int WMAX = Cfg::WMAX, MW = mask_words(WMAX);
     float2 *D;
     float4 *H;
-    uint8_t *F, *R, *B;
+    unsigned *M, *B;
+    float2 *S;
     __device__ __forceinline__ explicit TileSmem(unsigned char *base)
     {
         D = reinterpret_cast<float2 *>(base);
         H = reinterpret_cast<float4 *>(D + WMAX);
-        F = reinterpret_cast<uint8_t *>(H + groups(NF) * WMAX);
-        R = F + WMAX;
-        B = R + WMAX;
+        S = reinterpret_cast<float2 *>(H + groups(NF) * WMAX);
+        M = reinterpret_cast<unsigned *>(S + Cfg::TX * Cfg::TY);
+        B = M + NF * MW;
     }
 };
+
+// Start element of target (jx, jy): one fixed-point step s <- j - D(s) from s0 = j - D_j, with D(s0)
+// interpolated bilinearly in the staged window (the walk still decides); floor(s0) when not staged.
+__device__ __forceinline__ void refined_start(const Win &w, const float2 *sD, bool staged, int jx, int jy, float2 s0,
+                                              int &ex, int &ey)
+{
+    ex = (int)floorf(s0.x);
+    ey = (int)floorf(s0.y);
+    if (!staged) return;
+    const int i0 = w.at(ex, ey);
+    const float fx = s0.x - (float)ex, fy = s0.y - (float)ey;
+    const float2 d00 = sD[i0], d10 = sD[i0 + 1], d01 = sD[i0 + w.wx], d11 = sD[i0 + w.wx + 1];
+    const float bx = fmaf(fx, d10.x - d00.x, d00.x), by = fmaf(fx, d10.y - d00.y, d00.y);
+    const float dx = fmaf(fy, fmaf(fx, d11.x - d01.x, d01.x) - bx, bx);
+    const float dy = fmaf(fy, fmaf(fx, d11.y - d01.y, d01.y) - by, by);
+    const float rx = (float)jx - dx, ry = (float)jy - dy;
+    if (finite_t(rx) && finite_t(ry) && fabsf(rx - s0.x) < 4.f && fabsf(ry - s0.y) < 4.f) {
+        ex = (int)floorf(rx);
+        ey = (int)floorf(ry);
+    }
+}
+
+// Result of one target on the general path (for the counters).
+struct TargetOut {
+    int st, hops, iters, f64, nlin;
+};
+
+// The general path of one target (rare: out of line so that the fast path carries none of its
+// code or registers): the walk of walk2 from the refined start with global reads where the window
+// ends, the FP64 re-solve of a failed or nearly degenerate FP32 inversion (from the first start
+// element when the FP32 walk got lost or folded), then order and sum from shared memory when the
+// element's stencil is staged and from global memory otherwise.  A target that still fails keeps
+// its old values (the fail policy is applied by the host).
+template <int NF>
+__device__ __noinline__ TargetOut slow_target(const TileArgs &a, const Win w, const float2 *sD, const float4 *sH,
+                                              int gstride, const unsigned *sB, bool limit, long long jj, int jx,
+                                              int jy, int ex, int ey, int c0x, int c0y)
+{
+    TargetOut r = {ST_OK, 0, 0, 0, 0};
+    float xf[3] = {0.f, 0.f, 0.f};
+    bool degen = false;
+    int st = walk2<float>(a, w, sD, jx, jy, ex, ey, xf, r.hops, r.iters, degen);
+    float xi0 = xf[0], xi1 = xf[1];
+    if (st != ST_OK || degen) {
+        if (st == ST_LOCATE || st == ST_FOLD) {
+            ex = c0x;
+            ey = c0y;
+        }
+        double xd[3] = {0.0, 0.0, 0.0};
+        bool dg = false;
+        st = walk2<double>(a, w, sD, jx, jy, ex, ey, xd, r.hops, r.iters, dg);
+        xi0 = (float)xd[0];
+        xi1 = (float)xd[1];
+        r.f64 = 1;
+    }
+    r.st = st;
+    if (st != ST_OK) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a.out[f][jj] = __ldg(a.in[f] + jj);
+        return r;
+    }
+    const int rx = ex - w.lox, ry = ey - w.loy;
+    const bool fast = rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;  // false when not staged
+    unsigned lin_mask = a.max_order == 0 ? 0xffu : 0u;
+    if (limit) {
+        if (fast) {
+            const int nwx = (w.wx + 31) >> 5;
+            const unsigned *b = sB + ry * nwx + (rx >> 5);
+            lin_mask = 0u;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) lin_mask |= ((b[f * w.wy * nwx] >> (rx & 31)) & 1u) << f;
+        } else {
+            lin_mask = box_flags_global(a, ex, ey);
+        }
+    }
+    r.nlin = __popc(lin_mask & ((1u << NF) - 1u));
+    if (fast) {
+        float wc[2][4];
+        cubic_weights(xi0, wc[0]);
+        cubic_weights(xi1, wc[1]);
+        const int o = (ry - 1) * w.wx + (rx - 1);
+        store_group<NF, 0>(a, jj, sH + o, w.wx, wc, xi0, xi1, lin_mask);
+        if constexpr (groups(NF) > 1) store_group<NF, 1>(a, jj, sH + gstride + o, w.wx, wc, xi0, xi1, lin_mask);
+    } else {
+        interp_global(a, jj, ex, ey, xi0, xi1, lin_mask);
+    }
+    return r;
+}
 
 // One TX x TY tile of targets with origin (x0, y0): every thread of the CTA calls this; it
 // synchronises the CTA.
 template <class Cfg, int NF, bool FUSED>
 __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0,
-                                             const TileSmem<NF, Cfg::WMAX> &sm, int *sBox, LocalCounters &cnt)
+                                             const TileSmem<Cfg, NF> &sm, int *sBox, LocalCounters &cnt)
 {
     constexpr int TX = Cfg::TX, NT = Cfg::NT, ROWS = Cfg::ROWS, TPT = Cfg::TPT, WMAX = Cfg::WMAX;
     constexpr int NG = groups(NF);
@@ -316,25 +429,24 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     if (threadIdx.x < 4) sBox[threadIdx.x] = (threadIdx.x < 2) ? INT_MAX : INT_MIN;
 
     // ---- phase 1: start elements floor(j - D_j) and their bounding box ----------------------
-    float sx[TPT], sy[TPT];
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
         const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
-        sx[k] = (float)jx;
-        sy[k] = (float)jy;
+        float2 s0 = make_float2((float)jx, (float)jy);
         if (jx < n0 && jy < n1) {
             const float2 d = __ldg(reinterpret_cast<const float2 *>(a.D) + (long long)jy * n0 + jx);
             const float ux = fminf(fmaxf((float)jx - d.x, (float)jx - 65536.f), (float)jx + 65536.f);
             const float uy = fminf(fmaxf((float)jy - d.y, (float)jy - 65536.f), (float)jy + 65536.f);
-            sx[k] = finite_t(ux) ? ux : (float)jx;
-            sy[k] = finite_t(uy) ? uy : (float)jy;
-            const int c0x = (int)floorf(sx[k]), c0y = (int)floorf(sy[k]);
+            s0.x = finite_t(ux) ? ux : (float)jx;
+            s0.y = finite_t(uy) ? uy : (float)jy;
+            const int c0x = (int)floorf(s0.x), c0y = (int)floorf(s0.y);
             mnx = min(mnx, c0x);
             mny = min(mny, c0y);
             mxx = max(mxx, c0x);
             mxy = max(mxy, c0y);
         }
+        sm.S[k * NT + threadIdx.x] = s0;
     }
     __syncthreads();
     mnx = __reduce_min_sync(0xffffffffu, mnx);
@@ -353,7 +465,11 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     Win w;
     const long long wxl = (long long)sBox[2] - sBox[0] + 2 * WALK_SLACK + 6;
     const long long wyl = (long long)sBox[3] - sBox[1] + 2 * WALK_SLACK + 6;
-    const bool staged = wxl > 0 && wyl > 0 && wxl <= WMAX && wyl <= WMAX && wxl * wyl <= WMAX;
+    // staged windows also lie within one period of the grid on each side, so that their nodes
+    // wrap with a compare (wrap_near)
+    const long long olx = (long long)sBox[0] - WALK_SLACK - 2, oly = (long long)sBox[1] - WALK_SLACK - 2;
+    const bool staged = wxl > 0 && wyl > 0 && wxl <= WMAX && wyl <= WMAX && wxl * wyl <= WMAX && olx >= -n0 &&
+                        oly >= -n1 && olx + wxl <= 2LL * n0 && oly + wyl <= 2LL * n1;
     w.lox = staged ? sBox[0] - WALK_SLACK - 2 : 0;
     w.loy = staged ? sBox[1] - WALK_SLACK - 2 : 0;
     w.wx = staged ? (int)wxl : 0;
@@ -365,22 +481,29 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     const float inv_wx = staged ? 1.f / (float)w.wx : 0.f;
     for (int q = threadIdx.x; q < nwin; q += NT) {
         const int wy = row_of(q, inv_wx), wx = q - wy * w.wx;
-        const long long gi = (long long)wrap_fast(w.loy + wy, n1) * n0 + wrap_fast(w.lox + wx, n0);
+        const long long gi = (long long)wrap_near(w.loy + wy, n1) * n0 + wrap_near(w.lox + wx, n0);
         cp_async<8>(sm.D + q, reinterpret_cast<const float2 *>(a.D) + gi);
 #pragma unroll
         for (int f = 0; f < NF; ++f) cp_async<4>(reinterpret_cast<float *>(sm.H + (f >> 2) * WMAX + q) + (f & 3), a.in[f] + gi);
+    }
+    // clear the flag plane while the copies are in flight
+    if (a.max_order >= 1 && a.thr >= 0.f) {
+        const int nm = NF * w.wy * ((w.wx + 31) >> 5);
+        for (int q = threadIdx.x; q < nm; q += NT) sm.M[q] = 0u;
     }
     cp_async_wait_all();
     __syncthreads();
 
     // ---- phase 3: jump flags (Sec. 2.3) and their OR over each element's 4x4 stencil ---------
+    // Flags of the interior nodes go to bit plane M (one bit per node and field, set with a
+    // shared-memory atomic: flagged nodes are few); then B = M ORed over 4 rows and bits x-1 .. x+2.
+    const int nwx = (w.wx + 31) >> 5, plane = w.wy * nwx;
     if (limit) {
-        // flags of the interior nodes (the limiter needs both neighbours on each axis)
         const int iw = w.wx - 2, ni = iw * (w.wy - 2);
         const float inv_iw = 1.f / (float)max(iw, 1);
         for (int q = threadIdx.x; q < ni; q += NT) {
-            const int r = row_of(q, inv_iw);
-            const int idx = (r + 1) * w.wx + (q - r * iw) + 1;
+            const int r = row_of(q, inv_iw), y = r + 1, x = q - r * iw + 1;
+            const int idx = y * w.wx + x;
             unsigned bits = 0;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
@@ -399,90 +522,76 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
                     bits |= (jump4<1>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<1>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
                             << (4 * g);
             }
-            sm.F[idx] = (uint8_t)bits;
+            if (bits) {
+                unsigned *m = sm.M + y * nwx + (x >> 5);
+                const unsigned bit = 1u << (x & 31);
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    if ((bits >> f) & 1u) atomicOr(m + f * plane, bit);
+            }
         }
         __syncthreads();
-        // OR along x over c-1 .. c+2 for rows 1 .. wy-2, columns 2 .. wx-4
-        const int rw = w.wx - 5, nr = rw * (w.wy - 2);
-        const float inv_rw = 1.f / (float)max(rw, 1);
-        for (int q = threadIdx.x; q < nr; q += NT) {
-            const int r = row_of(q, inv_rw);
-            const int idx = (r + 1) * w.wx + (q - r * rw) + 2;
-            sm.R[idx] = sm.F[idx - 1] | sm.F[idx] | sm.F[idx + 1] | sm.F[idx + 2];
-        }
-        __syncthreads();
-        // OR along y: the element's 4x4 stencil, rows 2 .. wy-4
-        const int nb = rw * (w.wy - 5);
-        for (int q = threadIdx.x; q < nb; q += NT) {
-            const int r = row_of(q, inv_rw);
-            const int idx = (r + 2) * w.wx + (q - r * rw) + 2;
-            sm.B[idx] = sm.R[idx - w.wx] | sm.R[idx] | sm.R[idx + w.wx] | sm.R[idx + 2 * w.wx];
+        // rows 2 .. wy-4 (the elements whose stencil lies in the interior rows 1 .. wy-2)
+        const int brows = w.wy - 5;
+        const float inv_b = 1.f / (float)max(brows, 1);
+        for (int q = threadIdx.x; q < NF * brows; q += NT) {
+            const int f = row_of(q, inv_b), y = q - f * brows + 2;
+            const unsigned *m = sm.M + f * plane + (y - 1) * nwx;
+            unsigned *b = sm.B + f * plane + y * nwx;
+            unsigned vp = 0u, vc = m[0] | m[nwx] | m[2 * nwx] | m[3 * nwx];
+            for (int kw = 0; kw < nwx; ++kw) {
+                const int k1 = kw + 1;
+                const unsigned vn = k1 < nwx ? (m[k1] | m[nwx + k1] | m[2 * nwx + k1] | m[3 * nwx + k1]) : 0u;
+                b[kw] = vc | __funnelshift_l(vp, vc, 1) | __funnelshift_r(vc, vn, 1) | __funnelshift_r(vc, vn, 2);
+                vp = vc;
+                vc = vn;
+            }
         }
         __syncthreads();
     }
 
     // ---- phase 4: per target: search, Newton, order, tensor Z-spline sum ---------------------
+    // Targets that leave the fast path are marked and finished after the loop, so that the loop
+    // carries no call.
     if (!staged && threadIdx.x == 0) cnt.fallback += 1;
+    unsigned slow = 0u;
 #pragma unroll 1
     for (int k = 0; k < TPT; ++k) {
         const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
         if (jx >= n0 || jy >= n1) continue;
         const long long jj = (long long)jy * n0 + jx;
-        // start element: one fixed-point step s <- j - D(s) from s0 = j - D_j, with D(s0)
-        // interpolated bilinearly in the staged window (the walk below still decides)
-        int ex = (int)floorf(sx[k]), ey = (int)floorf(sy[k]);
-        const int c0x = ex, c0y = ey;
-        if (staged) {
-            const int i0 = w.at(ex, ey);
-            const float fx = sx[k] - (float)ex, fy = sy[k] - (float)ey;
-            const float2 d00 = sm.D[i0], d10 = sm.D[i0 + 1], d01 = sm.D[i0 + w.wx], d11 = sm.D[i0 + w.wx + 1];
-            const float dx = fmaf(fy, fmaf(fx, d11.x - d01.x, d01.x) - fmaf(fx, d10.x - d00.x, d00.x), fmaf(fx, d10.x - d00.x, d00.x));
-            const float dy = fmaf(fy, fmaf(fx, d11.y - d01.y, d01.y) - fmaf(fx, d10.y - d00.y, d00.y), fmaf(fx, d10.y - d00.y, d00.y));
-            const float rx_ = (float)jx - dx, ry_ = (float)jy - dy;
-            if (finite_t(rx_) && finite_t(ry_) && fabsf(rx_ - sx[k]) < 4.f && fabsf(ry_ - sy[k]) < 4.f) {
-                ex = (int)floorf(rx_);
-                ey = (int)floorf(ry_);
-            }
-        }
+        int ex, ey;
+        refined_start(w, sm.D, staged, jx, jy, sm.S[k * NT + threadIdx.x], ex, ey);
         int hops = 0, iters = 0;
-        float xf[3] = {0.f, 0.f, 0.f};
-        bool degen = false;
-        int st = walk2<float>(a, w, sm.D, jx, jy, ex, ey, xf, hops, iters, degen);
-        float xi0 = xf[0], xi1 = xf[1];
-        if (st != ST_OK || degen) {
-            st = resolve_f64(a, w, sm.D, jx, jy, st, c0x, c0y, ex, ey, xi0, xi1, hops, iters);
-            cnt.f64 += 1;
-        }
-        cnt.targets += 1;
-        cnt.hops += hops;
-        cnt.hops_max = max(cnt.hops_max, (unsigned)hops);
-        cnt.iters += iters;
-        cnt.iters_max = max(cnt.iters_max, (unsigned)iters);
-        if (st != ST_OK) {
-            cnt.fl += st == ST_LOCATE;
-            cnt.fn += st == ST_NEWTON;
-            cnt.ff += st == ST_FOLD;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) a.out[f][jj] = __ldg(a.in[f] + jj);
-        } else {
-            const int rx = ex - w.lox, ry = ey - w.loy;
-            const bool fast = rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;  // false when not staged
+        float xi0 = 0.f, xi1 = 0.f;
+        bool ok = staged && walk_window(w, sm.D, a.walk_max, a.max_iter, jx, jy, ex, ey, xi0, xi1, hops, iters);
+        const int rx = ex - w.lox, ry = ey - w.loy;
+        ok = ok && rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;
+        if (ok) {
+            cnt.targets += 1;
+            cnt.hops += hops;
+            cnt.hops_max = max(cnt.hops_max, (unsigned)hops);
+            cnt.iters += iters;
+            cnt.iters_max = max(cnt.iters_max, (unsigned)iters);
             // Sec. 2.3: fields flagged anywhere in the element's 4x4 stencil drop to linear
             unsigned lin_mask = a.max_order == 0 ? 0xffu : 0u;
-            if (limit) lin_mask = fast ? (unsigned)sm.B[ry * w.wx + rx] : box_flags_global(a, ex, ey);
+            if (limit) {
+                const unsigned *b = sm.B + ry * nwx + (rx >> 5);
+                lin_mask = 0u;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) lin_mask |= ((b[f * plane] >> (rx & 31)) & 1u) << f;
+            }
             const unsigned nlin = __popc(lin_mask & ((1u << NF) - 1u));
             cnt.oh0 += nlin;
             cnt.oh1 += NF - nlin;
-            if (fast) {
-                float wc[2][4];
-                cubic_weights(xi0, wc[0]);
-                cubic_weights(xi1, wc[1]);
-                const int o = (ry - 1) * w.wx + (rx - 1);
-                store_group<NF, 0>(a, jj, sm.H + o, w.wx, wc, xi0, xi1, lin_mask);
-                if constexpr (NG > 1) store_group<NF, 1>(a, jj, sm.H + WMAX + o, w.wx, wc, xi0, xi1, lin_mask);
-            } else {
-                interp_global(a, jj, ex, ey, xi0, xi1, lin_mask);
-            }
+            float wc[2][4];
+            cubic_weights(xi0, wc[0]);
+            cubic_weights(xi1, wc[1]);
+            const int o = (ry - 1) * w.wx + (rx - 1);
+            store_group<NF, 0>(a, jj, sm.H + o, w.wx, wc, xi0, xi1, lin_mask);
+            if constexpr (NG > 1) store_group<NF, 1>(a, jj, sm.H + WMAX + o, w.wx, wc, xi0, xi1, lin_mask);
+        } else {
+            slow |= 1u << k;
         }
         if (FUSED && a.D_next != nullptr) {
             float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
@@ -490,14 +599,39 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
             reinterpret_cast<float2 *>(a.D_next)[jj] = make_float2(d[0], d[1]);
         }
     }
+#pragma unroll 1
+    for (int k = 0; slow != 0u; ++k, slow >>= 1) {
+        if (!(slow & 1u)) continue;
+        const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
+        const long long jj = (long long)jy * n0 + jx;
+        const float2 s0 = sm.S[k * NT + threadIdx.x];
+        int ex, ey;
+        refined_start(w, sm.D, staged, jx, jy, s0, ex, ey);
+        const TargetOut r = slow_target<NF>(a, w, sm.D, sm.H, WMAX, sm.B, limit, jj, jx, jy, ex, ey,
+                                            (int)floorf(s0.x), (int)floorf(s0.y));
+        cnt.targets += 1;
+        cnt.hops += r.hops;
+        cnt.hops_max = max(cnt.hops_max, (unsigned)r.hops);
+        cnt.iters += r.iters;
+        cnt.iters_max = max(cnt.iters_max, (unsigned)r.iters);
+        cnt.f64 += r.f64;
+        if (r.st != ST_OK) {
+            cnt.fl += r.st == ST_LOCATE;
+            cnt.fn += r.st == ST_NEWTON;
+            cnt.ff += r.st == ST_FOLD;
+        } else {
+            cnt.oh0 += r.nlin;
+            cnt.oh1 += NF - r.nlin;
+        }
+    }
 }
 
 template <class Cfg, int NF, bool FUSED>
-__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const TileArgs a, const VelArgs<float> vn)
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const __grid_constant__ TileArgs a, const VelArgs<float> vn)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sBox[4];
-    const TileSmem<NF, Cfg::WMAX> sm(smem);
+    const TileSmem<Cfg, NF> sm(smem);
     LocalCounters cnt;
     cnt.clear();
     process_tile<Cfg, NF, FUSED>(a, vn, blockIdx.x * Cfg::TX, blockIdx.y * Cfg::TY, sm, sBox, cnt);
@@ -507,7 +641,8 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const
 template <class Cfg>
 __host__ size_t tile_smem_bytes(int nfields)
 {
-    return (size_t)Cfg::WMAX * (sizeof(float2) + sizeof(float4) * (size_t)((nfields + 3) / 4) + 3);
+    return (size_t)Cfg::WMAX * (sizeof(float2) + sizeof(float4) * (size_t)((nfields + 3) / 4)) +
+           sizeof(float2) * (size_t)(Cfg::TX * Cfg::TY) + 2 * sizeof(unsigned) * (size_t)nfields * (size_t)mask_words(Cfg::WMAX);
 }
 
 __host__ inline TileArgs make_tile_args(const sl_grid *g, const void *D, void *D_next, const void *const *in,
