@@ -92,8 +92,10 @@ typedef struct {
     int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
     int walk_start;                 /* SL_START_BACKWARD (from j - D_j) or SL_START_PAPER (Sec. 2.2) */
     int kernel;                     /* SL_KERNEL_AUTO, SL_KERNEL_GENERIC or SL_KERNEL_TILED           */
-    int tile_config;                /* 2-D FP32 tiles: 0 default (= 1), 1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16
-                                       compiled for 4 CTAs per SM                                 */
+    int tile_config;                /* 2-D FP32 tiles: 0 default (= 5), 1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16
+                                       compiled for 4 CTAs per SM, 5: 32x32 pipelined (persistent,
+                                       one CTA per SM staging the next tiles while it computes;
+                                       1 above 4 fields; batches run 5 as 1)                      */
 } sl_grid_desc;
 
 /* Counters accumulated on the device since creation or the last sl_reset_diagnostics. */
@@ -143,7 +145,9 @@ sl_status sl_remap_fields_debug(sl_grid *grid, const void *const *in, void *cons
 
 /* nsteps full steps (flags, advect, remap, reset) starting at time t0.  `fields`: nfields device
  * planes, updated in place; `scratch`: nfields device planes of the same size used as the other
- * half of a ping-pong pair (contents undefined afterwards). */
+ * half of a ping-pong pair (contents undefined afterwards).  On the fused FP32 path the grid's
+ * current D afterwards holds the displacement of the step that follows (t0 + nsteps*dt), and a
+ * next call starting there with the same dt does not integrate it again. */
 sl_status sl_step(sl_grid *grid, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
                   void *stream);
 
@@ -181,7 +185,7 @@ sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], co
  * aligned); the library allocates no device memory. */
 typedef struct sl_batch sl_batch;
 
-/* Workspace bytes of a batch of these grids with tile configuration tile_config (0..4, as in
+/* Workspace bytes of a batch of these grids with tile configuration tile_config (0..5, as in
  * sl_grid_desc); 0 if a grid is not eligible. */
 size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config);
 

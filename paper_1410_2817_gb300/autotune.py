@@ -1,7 +1,8 @@
 """Tile-shape autotuning for the 2-D FP32 kernels.
 
-The tiled kernels are compiled for four tile configurations (1: 32x32, 2: 32x16, 3: 64x16
-targets per CTA, 4: 32x16 with registers budgeted for 4 CTAs per SM).  Which one is fastest
+The tiled kernels are compiled for five tile configurations (1: 32x32, 2: 32x16, 3: 64x16
+targets per CTA, 4: 32x16 with registers budgeted for 4 CTAs per SM, 5: 32x32 on a persistent CTA
+per SM that stages its next tiles while it computes).  Which one is fastest
 depends on the grid sizes (ragged edge tiles, number of CTAs against 152 SMs) and on how far the
 flow moves nodes (window size).  The tuner times each
 configuration on the caller's own workload through the public API (CUDA events, after warm-up)
@@ -16,7 +17,7 @@ import torch
 
 from . import sl
 
-CONFIGS = (1, 2, 3, 4)
+CONFIGS = (1, 2, 3, 4, 5)
 
 
 def _time(fn: Callable[[], None], repeats: int, warmup: int, stream) -> float:

@@ -220,7 +220,7 @@ static bool batch_eligible(const sl_grid *g)
 
 extern "C" size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config)
 {
-    if (!grids || count < 1 || tile_config < 0 || tile_config > 4) return 0;
+    if (!grids || count < 1 || tile_config < 0 || tile_config > 5) return 0;
     long long nitems = 0;
     for (int q = 0; q < count; ++q) {
         if (!batch_eligible(grids[q])) return 0;
@@ -239,7 +239,7 @@ extern "C" sl_status sl_batch_create(sl_grid *const *grids, int count, void *con
     if (!out) return SL_ERR_ARG;
     *out = nullptr;
     if (!grids || count < 1 || !fields || !scratch || !t0 || !dt || !dev_workspace) return SL_ERR_ARG;
-    if (tile_config < 0 || tile_config > 4) return SL_ERR_ARG;
+    if (tile_config < 0 || tile_config > 5) return SL_ERR_ARG;
     if (((uintptr_t)dev_workspace & 255u) != 0) return SL_ERR_ARG;
     const int nf = grids[0] ? grids[0]->nfields : 0;
     if (nf < 1 || nf > 4) return SL_ERR_UNSUPPORTED;

@@ -30,6 +30,11 @@ struct sl_grid {
     int steady;
     int d_cached;
     double d_cached_dt;
+    // The fused FP32 path integrates, inside a call's last remap, the displacement of the step
+    // that follows the call: next_valid says D[dcur] holds it for the velocity arguments next_vel,
+    // so a call that starts there skips its own integration.
+    int next_valid;
+    VelArgs<float> next_vel;
 };
 
 #define SL_MOMENT_BLOCKS 512
@@ -66,7 +71,10 @@ cudaError_t launch_tiled2d_cfgb(const sl_grid *g, const void *D, void *D_next, d
                                 const void *const *in, void *const *out, cudaStream_t s);
 cudaError_t launch_tiled2d_cfgc(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                                 const void *const *in, void *const *out, cudaStream_t s);
+cudaError_t launch_tiled2d_cfgp(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
+                                const void *const *in, void *const *out, cudaStream_t s);
 size_t tiled2d_smem_bytes_cfga(int nfields);
+size_t tiled2d_smem_bytes_cfgp(int nfields);
 size_t tiled2d_smem_bytes_cfgb(int nfields);
 size_t tiled2d_smem_bytes_cfgc(int nfields);
 cudaError_t launch_tiled2d_cfgd(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,

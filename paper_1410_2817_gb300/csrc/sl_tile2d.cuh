@@ -18,6 +18,7 @@
 // nodes: the velocity is given, so D(t + dt) does not depend on the fields being remapped.
 #pragma once
 
+#include <algorithm>
 #include <limits.h>
 #include <math.h>
 #include <string.h>
@@ -41,6 +42,7 @@ typedef TileCfg<32, 32, 256, 8> CfgA;  // default
 typedef TileCfg<32, 16, 256, 8> CfgB;
 typedef TileCfg<64, 16, 256, 8> CfgC;
 typedef TileCfg<32, 16, 256, 8, 4> CfgD;  // 4 CTAs per SM: at most 64 registers per thread
+typedef TileCfg<32, 32, 512, 8, 1> CfgP;  // pipelined, one CTA of 16 warps per SM
 
 constexpr int WALK_SLACK = 1;          // elements the walk may step beyond the start-cell box
 
@@ -416,84 +418,95 @@ __device__ __noinline__ TargetOut slow_target(const TileArgs &a, const Win w, co
     return r;
 }
 
-// One TX x TY tile of targets with origin (x0, y0): every thread of the CTA calls this; it
-// synchronises the CTA.
-template <class Cfg, int NF, bool FUSED>
-__device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0,
-                                             const TileSmem<Cfg, NF> &sm, int *sBox, LocalCounters &cnt)
+// Start point j - D_j of a target, clamped so that garbage displacements cannot overflow the walk.
+__device__ __forceinline__ float2 start_point(int jx, int jy, float2 d)
 {
-    constexpr int TX = Cfg::TX, NT = Cfg::NT, ROWS = Cfg::ROWS, TPT = Cfg::TPT, WMAX = Cfg::WMAX;
-    constexpr int NG = groups(NF);
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int n0 = a.n0, n1 = a.n1;
-    if (threadIdx.x < 4) sBox[threadIdx.x] = (threadIdx.x < 2) ? INT_MAX : INT_MIN;
+    const float ux = fminf(fmaxf((float)jx - d.x, (float)jx - 65536.f), (float)jx + 65536.f);
+    const float uy = fminf(fmaxf((float)jy - d.y, (float)jy - 65536.f), (float)jy + 65536.f);
+    return make_float2(finite_t(ux) ? ux : (float)jx, finite_t(uy) ? uy : (float)jy);
+}
 
-    // ---- phase 1: start elements floor(j - D_j) and their bounding box ----------------------
-    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-        const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
-        float2 s0 = make_float2((float)jx, (float)jy);
-        if (jx < n0 && jy < n1) {
-            const float2 d = __ldg(reinterpret_cast<const float2 *>(a.D) + (long long)jy * n0 + jx);
-            const float ux = fminf(fmaxf((float)jx - d.x, (float)jx - 65536.f), (float)jx + 65536.f);
-            const float uy = fminf(fmaxf((float)jy - d.y, (float)jy - 65536.f), (float)jy + 65536.f);
-            s0.x = finite_t(ux) ? ux : (float)jx;
-            s0.y = finite_t(uy) ? uy : (float)jy;
-            const int c0x = (int)floorf(s0.x), c0y = (int)floorf(s0.y);
-            mnx = min(mnx, c0x);
-            mny = min(mny, c0y);
-            mxx = max(mxx, c0x);
-            mxy = max(mxy, c0y);
-        }
-        sm.S[k * NT + threadIdx.x] = s0;
-    }
-    __syncthreads();
+// Window of a tile from the box [bx0, bx1] x [by0, by1] of its start elements: widened by the walk
+// slack, the cubic stencil (c-1 .. c+2) and the limiter's neighbours (one more node each side).
+// A window is staged when it fits WMAX nodes and lies within one period of the grid on each side
+// (so that its nodes wrap with wrap_near); otherwise the tile runs on global memory.
+template <int WMAX>
+__device__ __forceinline__ Win window_of(int bx0, int by0, int bx1, int by1, int n0, int n1, bool &staged)
+{
+    const long long wxl = (long long)bx1 - bx0 + 2 * WALK_SLACK + 6;
+    const long long wyl = (long long)by1 - by0 + 2 * WALK_SLACK + 6;
+    const long long olx = (long long)bx0 - WALK_SLACK - 2, oly = (long long)by0 - WALK_SLACK - 2;
+    staged = wxl > 0 && wyl > 0 && wxl <= WMAX && wyl <= WMAX && wxl * wyl <= WMAX && olx >= -n0 && oly >= -n1 &&
+             olx + wxl <= 2LL * n0 && oly + wyl <= 2LL * n1;
+    Win w;
+    w.lox = staged ? (int)olx : 0;
+    w.loy = staged ? (int)oly : 0;
+    w.wx = staged ? (int)wxl : 0;
+    w.wy = staged ? (int)wyl : 0;
+    return w;
+}
+
+// Box of the CTA's start elements: warp reductions, then shared atomics into box (reset by the
+// caller beforehand); returns after a barrier with the box read back.
+__device__ __forceinline__ void reduce_box(int mnx, int mny, int mxx, int mxy, int *box, int &bx0, int &by0, int &bx1,
+                                           int &by1)
+{
     mnx = __reduce_min_sync(0xffffffffu, mnx);
     mny = __reduce_min_sync(0xffffffffu, mny);
     mxx = __reduce_max_sync(0xffffffffu, mxx);
     mxy = __reduce_max_sync(0xffffffffu, mxy);
     if ((threadIdx.x & 31) == 0) {
-        atomicMin(&sBox[0], mnx);
-        atomicMin(&sBox[1], mny);
-        atomicMax(&sBox[2], mxx);
-        atomicMax(&sBox[3], mxy);
+        atomicMin(&box[0], mnx);
+        atomicMin(&box[1], mny);
+        atomicMax(&box[2], mxx);
+        atomicMax(&box[3], mxy);
     }
     __syncthreads();
-    // window: start-cell box widened by the walk slack, the cubic stencil (c-1 .. c+2) and the
-    // limiter's neighbours (one more node each side)
-    Win w;
-    const long long wxl = (long long)sBox[2] - sBox[0] + 2 * WALK_SLACK + 6;
-    const long long wyl = (long long)sBox[3] - sBox[1] + 2 * WALK_SLACK + 6;
-    // staged windows also lie within one period of the grid on each side, so that their nodes
-    // wrap with a compare (wrap_near)
-    const long long olx = (long long)sBox[0] - WALK_SLACK - 2, oly = (long long)sBox[1] - WALK_SLACK - 2;
-    const bool staged = wxl > 0 && wyl > 0 && wxl <= WMAX && wyl <= WMAX && wxl * wyl <= WMAX && olx >= -n0 &&
-                        oly >= -n1 && olx + wxl <= 2LL * n0 && oly + wyl <= 2LL * n1;
-    w.lox = staged ? sBox[0] - WALK_SLACK - 2 : 0;
-    w.loy = staged ? sBox[1] - WALK_SLACK - 2 : 0;
-    w.wx = staged ? (int)wxl : 0;
-    w.wy = staged ? (int)wyl : 0;
-    const bool limit = a.max_order >= 1 && a.thr >= 0.f;
+    bx0 = box[0];
+    by0 = box[1];
+    bx1 = box[2];
+    by1 = box[3];
+}
 
-    // ---- phase 2: stage displacements and fields of the window (all copies in flight) -------
+// Issue the asynchronous copies of a staged window: displacements to sD, fields (4 per float4,
+// group stride WMAX) to sH.  The caller waits for them (cp_async_wait_all + barrier).
+template <class Cfg, int NF>
+__device__ __forceinline__ void stage_window(const TileArgs &a, const Win &w, float2 *sD, float4 *sH)
+{
     const int nwin = w.wx * w.wy;
-    const float inv_wx = staged ? 1.f / (float)w.wx : 0.f;
-    for (int q = threadIdx.x; q < nwin; q += NT) {
+    const float inv_wx = nwin > 0 ? 1.f / (float)w.wx : 0.f;
+    for (int q = threadIdx.x; q < nwin; q += Cfg::NT) {
         const int wy = row_of(q, inv_wx), wx = q - wy * w.wx;
-        const long long gi = (long long)wrap_near(w.loy + wy, n1) * n0 + wrap_near(w.lox + wx, n0);
-        cp_async<8>(sm.D + q, reinterpret_cast<const float2 *>(a.D) + gi);
+        const long long gi = (long long)wrap_near(w.loy + wy, a.n1) * a.n0 + wrap_near(w.lox + wx, a.n0);
+        cp_async<8>(sD + q, reinterpret_cast<const float2 *>(a.D) + gi);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) cp_async<4>(reinterpret_cast<float *>(sm.H + (f >> 2) * WMAX + q) + (f & 3), a.in[f] + gi);
+        for (int f = 0; f < NF; ++f)
+            cp_async<4>(reinterpret_cast<float *>(sH + (f >> 2) * Cfg::WMAX + q) + (f & 3), a.in[f] + gi);
     }
-    // clear the flag plane while the copies are in flight
+}
+
+// Clear the flag plane of a window before its flags are set.
+template <class Cfg, int NF>
+__device__ __forceinline__ void clear_flags(const TileArgs &a, const Win &w, unsigned *M)
+{
     if (a.max_order >= 1 && a.thr >= 0.f) {
         const int nm = NF * w.wy * ((w.wx + 31) >> 5);
-        for (int q = threadIdx.x; q < nm; q += NT) sm.M[q] = 0u;
+        for (int q = threadIdx.x; q < nm; q += Cfg::NT) M[q] = 0u;
     }
-    cp_async_wait_all();
-    __syncthreads();
+}
 
+// Phases 3 and 4 of one tile whose window (sD, sH) and start points (sS) are in shared memory and
+// whose flag plane M is clear: every thread of the CTA calls this; it synchronises the CTA.
+template <class Cfg, int NF, bool FUSED>
+__device__ __forceinline__ void tile_compute(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0, const Win &w,
+                                             bool staged, const float2 *sD, const float4 *sH, const float2 *sS,
+                                             unsigned *sM, unsigned *sB, LocalCounters &cnt)
+{
+    constexpr int TX = Cfg::TX, NT = Cfg::NT, ROWS = Cfg::ROWS, TPT = Cfg::TPT, WMAX = Cfg::WMAX;
+    constexpr int NG = groups(NF);
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int n0 = a.n0, n1 = a.n1;
+    const bool limit = a.max_order >= 1 && a.thr >= 0.f;
     // ---- phase 3: jump flags (Sec. 2.3) and their OR over each element's 4x4 stencil ---------
     // Flags of the interior nodes go to bit plane M (one bit per node and field, set with a
     // shared-memory atomic: flagged nodes are few); then B = M ORed over 4 rows and bits x-1 .. x+2.
@@ -507,7 +520,7 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
             unsigned bits = 0;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                const float4 *h = sm.H + g * WMAX;
+                const float4 *h = sH + g * WMAX;
                 const float4 c = h[idx];
                 if (in_group(NF, g) == 4)
                     bits |= (jump4<4>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<4>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
@@ -523,7 +536,7 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
                             << (4 * g);
             }
             if (bits) {
-                unsigned *m = sm.M + y * nwx + (x >> 5);
+                unsigned *m = sM + y * nwx + (x >> 5);
                 const unsigned bit = 1u << (x & 31);
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
@@ -536,8 +549,8 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
         const float inv_b = 1.f / (float)max(brows, 1);
         for (int q = threadIdx.x; q < NF * brows; q += NT) {
             const int f = row_of(q, inv_b), y = q - f * brows + 2;
-            const unsigned *m = sm.M + f * plane + (y - 1) * nwx;
-            unsigned *b = sm.B + f * plane + y * nwx;
+            const unsigned *m = sM + f * plane + (y - 1) * nwx;
+            unsigned *b = sB + f * plane + y * nwx;
             unsigned vp = 0u, vc = m[0] | m[nwx] | m[2 * nwx] | m[3 * nwx];
             for (int kw = 0; kw < nwx; ++kw) {
                 const int k1 = kw + 1;
@@ -561,10 +574,10 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
         if (jx >= n0 || jy >= n1) continue;
         const long long jj = (long long)jy * n0 + jx;
         int ex, ey;
-        refined_start(w, sm.D, staged, jx, jy, sm.S[k * NT + threadIdx.x], ex, ey);
+        refined_start(w, sD, staged, jx, jy, sS[k * NT + threadIdx.x], ex, ey);
         int hops = 0, iters = 0;
         float xi0 = 0.f, xi1 = 0.f;
-        bool ok = staged && walk_window(w, sm.D, a.walk_max, a.max_iter, jx, jy, ex, ey, xi0, xi1, hops, iters);
+        bool ok = staged && walk_window(w, sD, a.walk_max, a.max_iter, jx, jy, ex, ey, xi0, xi1, hops, iters);
         const int rx = ex - w.lox, ry = ey - w.loy;
         ok = ok && rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;
         if (ok) {
@@ -576,7 +589,7 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
             // Sec. 2.3: fields flagged anywhere in the element's 4x4 stencil drop to linear
             unsigned lin_mask = a.max_order == 0 ? 0xffu : 0u;
             if (limit) {
-                const unsigned *b = sm.B + ry * nwx + (rx >> 5);
+                const unsigned *b = sB + ry * nwx + (rx >> 5);
                 lin_mask = 0u;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) lin_mask |= ((b[f * plane] >> (rx & 31)) & 1u) << f;
@@ -588,8 +601,8 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
             cubic_weights(xi0, wc[0]);
             cubic_weights(xi1, wc[1]);
             const int o = (ry - 1) * w.wx + (rx - 1);
-            store_group<NF, 0>(a, jj, sm.H + o, w.wx, wc, xi0, xi1, lin_mask);
-            if constexpr (NG > 1) store_group<NF, 1>(a, jj, sm.H + WMAX + o, w.wx, wc, xi0, xi1, lin_mask);
+            store_group<NF, 0>(a, jj, sH + o, w.wx, wc, xi0, xi1, lin_mask);
+            if constexpr (NG > 1) store_group<NF, 1>(a, jj, sH + WMAX + o, w.wx, wc, xi0, xi1, lin_mask);
         } else {
             slow |= 1u << k;
         }
@@ -604,10 +617,10 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
         if (!(slow & 1u)) continue;
         const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
         const long long jj = (long long)jy * n0 + jx;
-        const float2 s0 = sm.S[k * NT + threadIdx.x];
+        const float2 s0 = sS[k * NT + threadIdx.x];
         int ex, ey;
-        refined_start(w, sm.D, staged, jx, jy, s0, ex, ey);
-        const TargetOut r = slow_target<NF>(a, w, sm.D, sm.H, WMAX, sm.B, limit, jj, jx, jy, ex, ey,
+        refined_start(w, sD, staged, jx, jy, s0, ex, ey);
+        const TargetOut r = slow_target<NF>(a, w, sD, sH, WMAX, sB, limit, jj, jx, jy, ex, ey,
                                             (int)floorf(s0.x), (int)floorf(s0.y));
         cnt.targets += 1;
         cnt.hops += r.hops;
@@ -626,6 +639,46 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     }
 }
 
+
+// One TX x TY tile of targets with origin (x0, y0), staged and computed in one pass: every thread
+// of the CTA calls this; it synchronises the CTA.
+template <class Cfg, int NF, bool FUSED>
+__device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0,
+                                             const TileSmem<Cfg, NF> &sm, int *sBox, LocalCounters &cnt)
+{
+    constexpr int TX = Cfg::TX, NT = Cfg::NT, ROWS = Cfg::ROWS, TPT = Cfg::TPT;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    if (threadIdx.x < 4) sBox[threadIdx.x] = (threadIdx.x < 2) ? INT_MAX : INT_MIN;
+
+    // ---- phase 1: start elements floor(j - D_j) and their bounding box ----------------------
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
+        float2 s0 = make_float2((float)jx, (float)jy);
+        if (jx < a.n0 && jy < a.n1) {
+            s0 = start_point(jx, jy, __ldg(reinterpret_cast<const float2 *>(a.D) + (long long)jy * a.n0 + jx));
+            mnx = min(mnx, (int)floorf(s0.x));
+            mny = min(mny, (int)floorf(s0.y));
+            mxx = max(mxx, (int)floorf(s0.x));
+            mxy = max(mxy, (int)floorf(s0.y));
+        }
+        sm.S[k * NT + threadIdx.x] = s0;
+    }
+    __syncthreads();
+    int bx0, by0, bx1, by1;
+    reduce_box(mnx, mny, mxx, mxy, sBox, bx0, by0, bx1, by1);
+    bool staged;
+    const Win w = window_of<Cfg::WMAX>(bx0, by0, bx1, by1, a.n0, a.n1, staged);
+
+    // ---- phase 2: stage displacements and fields of the window (all copies in flight) -------
+    stage_window<Cfg, NF>(a, w, sm.D, sm.H);
+    clear_flags<Cfg, NF>(a, w, sm.M);
+    cp_async_wait_all();
+    __syncthreads();
+    tile_compute<Cfg, NF, FUSED>(a, vn, x0, y0, w, staged, sm.D, sm.H, sm.S, sm.M, sm.B, cnt);
+}
+
 template <class Cfg, int NF, bool FUSED>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const __grid_constant__ TileArgs a, const VelArgs<float> vn)
 {
@@ -636,6 +689,108 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const
     cnt.clear();
     process_tile<Cfg, NF, FUSED>(a, vn, blockIdx.x * Cfg::TX, blockIdx.y * Cfg::TY, sm, sBox, cnt);
     flush_counters(cnt, a.counters);
+}
+
+// Pipelined persistent variant: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... and
+// overlaps the memory traffic of the next tiles with the arithmetic of the current one.  While
+// tile t is computed, the window of tile t + G is being copied into the other window slot and the
+// displacements of tile t + 2G's targets into a third start-point slot, so that every copy has a
+// whole tile of arithmetic to arrive in.
+template <class Cfg, int NF, bool FUSED>
+__global__ void __launch_bounds__(Cfg::NT, 1)
+    remap_pipe2d_kernel(const __grid_constant__ TileArgs a, const VelArgs<float> vn, int tiles_x, int ntiles)
+{
+    constexpr int TX = Cfg::TX, TY = Cfg::TY, NT = Cfg::NT, ROWS = Cfg::ROWS, TPT = Cfg::TPT, WMAX = Cfg::WMAX;
+    constexpr int NG = groups(NF), NTGT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sBox[2][4];
+    float2 *const sD = reinterpret_cast<float2 *>(smem);                 // 2 window slots
+    float4 *const sH = reinterpret_cast<float4 *>(sD + 2 * WMAX);         // 2 window slots
+    float2 *const sS = reinterpret_cast<float2 *>(sH + 2 * NG * WMAX);    // 3 start-point slots
+    unsigned *const sM = reinterpret_cast<unsigned *>(sS + 3 * NTGT);
+    unsigned *const sB = sM + NF * mask_words(WMAX);
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, G = (int)gridDim.x;
+    LocalCounters cnt;
+    cnt.clear();
+    if (threadIdx.x < 8) sBox[threadIdx.x >> 2][threadIdx.x & 3] = (threadIdx.x & 3) < 2 ? INT_MAX : INT_MIN;
+
+    // raw displacements of tile t's targets into start-point slot S (asynchronous)
+    auto fetch_targets = [&](int t, float2 *S) {
+        const int tr = t / tiles_x, x0 = (t - tr * tiles_x) * TX, y0 = tr * TY;
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
+            if (jx < a.n0 && jy < a.n1)
+                cp_async<8>(S + k * NT + threadIdx.x, reinterpret_cast<const float2 *>(a.D) + (long long)jy * a.n0 + jx);
+        }
+    };
+    // start points of tile t (in place in S) and its window; box is reset, the other box gets
+    // reset for the next call; contains a barrier
+    auto window = [&](int t, float2 *S, int *box, int *other, bool &staged) -> Win {
+        const int tr = t / tiles_x, x0 = (t - tr * tiles_x) * TX, y0 = tr * TY;
+        int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const int jx = x0 + tx, jy = y0 + ty + k * ROWS;
+            if (jx < a.n0 && jy < a.n1) {
+                const float2 s0 = start_point(jx, jy, S[k * NT + threadIdx.x]);
+                S[k * NT + threadIdx.x] = s0;
+                mnx = min(mnx, (int)floorf(s0.x));
+                mny = min(mny, (int)floorf(s0.y));
+                mxx = max(mxx, (int)floorf(s0.x));
+                mxy = max(mxy, (int)floorf(s0.y));
+            }
+        }
+        int bx0, by0, bx1, by1;
+        reduce_box(mnx, mny, mxx, mxy, box, bx0, by0, bx1, by1);
+        if (threadIdx.x < 4) other[threadIdx.x] = threadIdx.x < 2 ? INT_MAX : INT_MIN;
+        return window_of<WMAX>(bx0, by0, bx1, by1, a.n0, a.n1, staged);
+    };
+
+    const int t0 = blockIdx.x;
+    if (t0 < ntiles) {
+        fetch_targets(t0, sS);
+        if (t0 + G < ntiles) fetch_targets(t0 + G, sS + NTGT);
+        cp_async_wait_all();
+        __syncthreads();
+        bool st_cur;
+        Win w_cur = window(t0, sS, sBox[0], sBox[1], st_cur);
+        stage_window<Cfg, NF>(a, w_cur, sD, sH);
+        int s3 = 0;  // start-point slot of the current tile (i mod 3)
+        for (int i = 0;; ++i) {
+            const int t = t0 + i * G;
+            if (t >= ntiles) break;
+            const int tn = t + G, tnn = t + 2 * G, p = i & 1;
+            const int s3n = s3 == 2 ? 0 : s3 + 1, s3nn = s3n == 2 ? 0 : s3n + 1;
+            cp_async_wait_all();  // window of t, displacements of tn's targets
+            __syncthreads();      // ... visible to all; tile t - G finished
+            clear_flags<Cfg, NF>(a, w_cur, sM);
+            bool st_nxt = false;
+            Win w_nxt;
+            w_nxt.lox = w_nxt.loy = w_nxt.wx = w_nxt.wy = 0;
+            if (tn < ntiles) {
+                w_nxt = window(tn, sS + s3n * NTGT, sBox[p ^ 1], sBox[p], st_nxt);
+                stage_window<Cfg, NF>(a, w_nxt, sD + (p ^ 1) * WMAX, sH + (p ^ 1) * NG * WMAX);
+                if (tnn < ntiles) fetch_targets(tnn, sS + s3nn * NTGT);
+            } else {
+                __syncthreads();
+            }
+            const int tr = t / tiles_x;
+            tile_compute<Cfg, NF, FUSED>(a, vn, (t - tr * tiles_x) * TX, tr * TY, w_cur, st_cur, sD + p * WMAX,
+                                         sH + p * NG * WMAX, sS + s3 * NTGT, sM, sB, cnt);
+            w_cur = w_nxt;
+            st_cur = st_nxt;
+            s3 = s3n;
+        }
+    }
+    flush_counters(cnt, a.counters);
+}
+
+template <class Cfg>
+__host__ size_t pipe_smem_bytes(int nfields)
+{
+    return 2 * (size_t)Cfg::WMAX * (sizeof(float2) + sizeof(float4) * (size_t)((nfields + 3) / 4)) +
+           3 * sizeof(float2) * (size_t)(Cfg::TX * Cfg::TY) + 2 * sizeof(unsigned) * (size_t)nfields * (size_t)mask_words(Cfg::WMAX);
 }
 
 template <class Cfg>
@@ -703,6 +858,46 @@ __host__ cudaError_t launch_tiled_fused(const sl_grid *g, const TileArgs &a, con
     case 6: return launch_tiled_nf<Cfg, 6, FUSED>(g, a, vn, s);
     case 7: return launch_tiled_nf<Cfg, 7, FUSED>(g, a, vn, s);
     default: return launch_tiled_nf<Cfg, 8, FUSED>(g, a, vn, s);
+    }
+}
+
+template <class Cfg, int NF, bool FUSED>
+__host__ cudaError_t launch_pipe_nf(const sl_grid *g, const TileArgs &a, const VelArgs<float> &vn, cudaStream_t s)
+{
+    const size_t smem = pipe_smem_bytes<Cfg>(NF);
+    static bool configured[64] = {};
+    static int per_sm[64] = {};
+    cudaError_t e = allow_smem(remap_pipe2d_kernel<Cfg, NF, FUSED>, g->device, smem, configured);
+    if (e != cudaSuccess) return e;
+    if (per_sm[g->device & 63] == 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, remap_pipe2d_kernel<Cfg, NF, FUSED>, Cfg::NT, smem);
+        if (e != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        per_sm[g->device & 63] = n;
+    }
+    const long long tiles_x = (g->n[0] + Cfg::TX - 1) / Cfg::TX, tiles_y = (g->n[1] + Cfg::TY - 1) / Cfg::TY;
+    const long long ntiles = tiles_x * tiles_y;
+    const long long ctas = std::min(ntiles, (long long)g->num_sms * per_sm[g->device & 63]);
+    remap_pipe2d_kernel<Cfg, NF, FUSED><<<(unsigned)ctas, Cfg::NT, smem, s>>>(a, vn, (int)tiles_x, (int)ntiles);
+    return cudaGetLastError();
+}
+
+// one pipelined remap (fused: also D(t_next)) of a 2-D FP32 grid with at most 4 fields
+template <class Cfg>
+__host__ cudaError_t launch_pipe_cfg(const sl_grid *g, const void *D, void *D_next, double t_next, double dt,
+                                     bool fused, const void *const *in, void *const *out, cudaStream_t s)
+{
+    const TileArgs a = make_tile_args(g, D, D_next, in, out);
+    VelArgs<float> vn;
+    memset(&vn, 0, sizeof(vn));
+    if (fused) vn = make_vel_args<float>(g, t_next, dt);
+    switch (g->nfields) {
+    case 1: return fused ? launch_pipe_nf<Cfg, 1, true>(g, a, vn, s) : launch_pipe_nf<Cfg, 1, false>(g, a, vn, s);
+    case 2: return fused ? launch_pipe_nf<Cfg, 2, true>(g, a, vn, s) : launch_pipe_nf<Cfg, 2, false>(g, a, vn, s);
+    case 3: return fused ? launch_pipe_nf<Cfg, 3, true>(g, a, vn, s) : launch_pipe_nf<Cfg, 3, false>(g, a, vn, s);
+    case 4: return fused ? launch_pipe_nf<Cfg, 4, true>(g, a, vn, s) : launch_pipe_nf<Cfg, 4, false>(g, a, vn, s);
+    default: return cudaErrorNotSupported;
     }
 }
 

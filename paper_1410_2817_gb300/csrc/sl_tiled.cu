@@ -17,7 +17,7 @@ bool Launch<T>::tiled_supported(const sl_grid *g)
     const size_t smem = c == 2   ? tiled2d_smem_bytes_cfgb(g->nfields)
                         : c == 3 ? tiled2d_smem_bytes_cfgc(g->nfields)
                         : c == 4 ? tiled2d_smem_bytes_cfgd(g->nfields)
-                                 : tiled2d_smem_bytes_cfga(g->nfields);
+                                 : tiled2d_smem_bytes_cfga(g->nfields);  // 5 falls back to 1 above 4 fields
     return smem <= 200 * 1024;
 }
 
@@ -25,6 +25,9 @@ static cudaError_t launch_tiled2d(const sl_grid *g, const void *D, void *D_next,
                                   const void *const *in, void *const *out, cudaStream_t s)
 {
     switch (g->desc.tile_config) {
+    case 5:
+        if (g->nfields <= 4) return launch_tiled2d_cfgp(g, D, D_next, t_next, dt, fused, in, out, s);
+        return launch_tiled2d_cfga(g, D, D_next, t_next, dt, fused, in, out, s);
     case 2: return launch_tiled2d_cfgb(g, D, D_next, t_next, dt, fused, in, out, s);
     case 3: return launch_tiled2d_cfgc(g, D, D_next, t_next, dt, fused, in, out, s);
     case 4: return launch_tiled2d_cfgd(g, D, D_next, t_next, dt, fused, in, out, s);

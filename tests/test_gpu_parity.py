@@ -405,11 +405,19 @@ def _shear_displacement(n, a):
     return D
 
 
-@pytest.mark.parametrize("case", ["swirl", "smooth_ragged", "shear_fallback", "limiter_off", "order0"])
-def test_tiled_matches_generic_f32(sl, orc, case):
+@pytest.mark.parametrize("tile_config", [1, 5])
+@pytest.mark.parametrize("case", ["swirl", "smooth_ragged", "shear_fallback", "limiter_off", "order0", "many_tiles"])
+def test_tiled_matches_generic_f32(sl, orc, case, tile_config):
     rng = np.random.default_rng(21)
     max_order, thr = 1, 0.25
-    if case == "swirl":
+    if case == "many_tiles":
+        # more 32x32 tiles (21 x 17, ragged) than one per SM: the pipelined kernel stages the next
+        # tiles of each CTA while it computes the current one
+        n = (650, 530)
+        D = inputs.smooth_displacement(n, amplitude=0.4, seed=6, shift=(3.1, -2.6))
+        h = np.stack([inputs.swirl_fields(650)[0][:530, :650], (rng.uniform(size=(530, 650)) > 0.7) * 1.0,
+                      rng.standard_normal((530, 650)).cumsum(axis=0) * 0.05])
+    elif case == "swirl":
         n = (256, 256)
         og = _og(orc, 2, n, 3, velocity="swirl2d", params=[5.0])
         D, h = orc.advect(og, 0.9, 5 / 256), inputs.swirl_fields(256)
@@ -432,7 +440,8 @@ def test_tiled_matches_generic_f32(sl, orc, case):
     nf = h.shape[0]
     outs, diags = {}, {}
     for kname, kern in (("generic", sl.SL_KERNEL_GENERIC), ("tiled", sl.SL_KERNEL_TILED)):
-        g = _gpu_grid(sl, 2, n, nf, sl.SL_F32, max_order=max_order, threshold=thr, start="backward", kernel=kern)
+        g = _gpu_grid(sl, 2, n, nf, sl.SL_F32, max_order=max_order, threshold=thr, start="backward", kernel=kern,
+                      tile_config=tile_config)
         hin = torch.tensor(h, dtype=torch.float32, device=DEV)
         hout = torch.empty_like(hin)
         g.set_displacement(torch.tensor(D, dtype=torch.float32, device=DEV))
@@ -479,16 +488,35 @@ def test_fused_step_matches_split_steps_f32(sl):
         f = fg
         t += wl.dt
     assert worst <= 2e-6, worst
-    # two fused steps: the second remap used the D the first launch integrated for t0 + dt
+    # two fused steps: the second remap used the D the first launch integrated for t0 + dt, and
+    # the second launch leaves D for the step after the call (t0 + 2 dt)
     ft = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
     gt.step(ft, torch.empty_like(ft), 0.25, wl.dt, 2)
     d_fused = gt.get_displacement()
-    gg.advect(0.25 + wl.dt, wl.dt)
+    gg.advect(0.25 + wl.dt + wl.dt, wl.dt)
     d_plain = gg.get_displacement()
     assert float((d_fused - d_plain).abs().max()) <= 1e-6 * float(d_plain.abs().max())
     l0 = gt.diagnostics()["kernel_launches"]
     gt.step(ft, torch.empty_like(ft), 0.0, wl.dt, 6)
     assert gt.diagnostics()["kernel_launches"] - l0 == 1 + 6  # one advect, then one launch per step
+    # a call that starts where the last one ended reuses the displacement it left ...
+    l0 = gt.diagnostics()["kernel_launches"]
+    f_chain = ft.clone()
+    gt.step(f_chain, torch.empty_like(ft), 0.0 + 5 * wl.dt + wl.dt, wl.dt, 3)
+    assert gt.diagnostics()["kernel_launches"] - l0 == 3
+    # ... and gives what a fresh integration gives
+    gf = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_AUTO)
+    f_fresh = ft.clone()
+    gf.step(f_fresh, torch.empty_like(ft), 0.0 + 5 * wl.dt + wl.dt, wl.dt, 3)
+    torch.cuda.synchronize()
+    # (the advect kernel and the fused launch run the same RK4 code; allow last-ulp contraction
+    # differences between the two compilations)
+    assert float((f_chain - f_fresh).abs().max()) <= 1e-5 * max(1.0, float(f_fresh.abs().max()))
+    # a displacement set by the caller is never taken for the carried one
+    gt.set_displacement(torch.zeros_like(d_fused))
+    l0 = gt.diagnostics()["kernel_launches"]
+    gt.step(ft, torch.empty_like(ft), 0.0 + 8 * wl.dt + wl.dt, wl.dt, 1)
+    assert gt.diagnostics()["kernel_launches"] - l0 == 2
 
 
 @pytest.mark.parametrize("case", ["deform3d_32", "ragged3d", "limiter_off3d"])
