@@ -142,18 +142,41 @@ __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D
 }
 
 // FP64 re-solve of a target whose FP32 inversion failed or whose element is nearly degenerate
-// (rare: out of line so that it costs the main path no registers)
-__device__ __noinline__ int resolve3_f64(const Geo3 &g, const float4 *__restrict__ D, int max_iter, int walk_max,
-                                         const int j[3], const int c0[3], int st32, int c[3], float xf[3], int &hops,
-                                         int &iters)
+// (rare: out of line, arguments and result by value, so that the main path keeps its element and
+// coordinates in registers)
+struct Resolve3 {
+    int st, c0, c1, c2;
+    float x0, x1, x2;
+    int hops, iters;
+};
+
+__device__ __noinline__ Resolve3 resolve3_f64(const float4 *__restrict__ D, int n0, int n1, int n2, int max_iter,
+                                              int walk_max, int j0, int j1, int j2, int st32, int cx, int cy, int cz,
+                                              int sx, int sy, int sz)
 {
+    const Geo3 g = {n0, n1, n2};
+    const int j[3] = {j0, j1, j2};
+    int c[3] = {cx, cy, cz};
+    if (st32 == ST_LOCATE || st32 == ST_FOLD) {
+        c[0] = sx;
+        c[1] = sy;
+        c[2] = sz;
+    }
     double xd[3] = {0.0, 0.0, 0.0};
     bool degd = false;
-    if (st32 == ST_LOCATE || st32 == ST_FOLD)
-        for (int q = 0; q < 3; ++q) c[q] = c0[q];
+    int hops = 0, iters = 0;
     const int st = walk3<double>(g, D, max_iter, walk_max, j, c, xd, hops, iters, &degd);
-    for (int q = 0; q < 3; ++q) xf[q] = (float)xd[q];
-    return st;
+    Resolve3 r;
+    r.st = st;
+    r.c0 = c[0];
+    r.c1 = c[1];
+    r.c2 = c[2];
+    r.x0 = (float)xd[0];
+    r.x1 = (float)xd[1];
+    r.x2 = (float)xd[2];
+    r.hops = hops;
+    r.iters = iters;
+    return r;
 }
 
 struct Blocked3Args {
@@ -167,50 +190,65 @@ struct Blocked3Args {
 };
 
 // eq. (multiZ) in 3-D for up to NFM fields: the 4x4x4 cubic (Z~1) sums and the trilinear (Z~0)
-// sums over the element's 8 vertices in one pass.  Row offsets are shared by all fields; with
-// XIN (the stencil does not cross the x seam) the 4 taps of a row sit at x0 .. x0+3.
+// sums over the element's 8 vertices in one pass.  Fields run in pairs on packed FP32x2 FMAs
+// (each lane rounds as fmaf does); row offsets (32-bit: the blocked kernel takes grids below 2^31
+// nodes) are shared by all fields; with XIN (the stencil does not cross the x seam) the 4 taps of
+// a row sit at x0 .. x0+3.
 template <int NFM, bool XIN>
-__device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4], const long long oy[4],
-                                         const long long oz[4], int x0, const float wc[3][4], const float xf[3],
+__device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4], const unsigned oy[4],
+                                         const unsigned oz[4], int x0, const float wc[3][4], const float xf[3],
                                          float cub[NFM], float lin[NFM])
 {
+    const float2 w0 = make_float2(wc[0][0], wc[0][0]), w1 = make_float2(wc[0][1], wc[0][1]);
+    const float2 w2 = make_float2(wc[0][2], wc[0][2]), w3 = make_float2(wc[0][3], wc[0][3]);
+    const float2 u0 = make_float2(1.f - xf[0], 1.f - xf[0]), u1 = make_float2(xf[0], xf[0]);
 #pragma unroll
-    for (int q = 0; q < NFM; ++q) cub[q] = lin[q] = 0.f;
+    for (int q = 0; q < NFM; q += 2) {
+        if (q >= a.nfields) break;
+        const float *ha = a.f.in[q];
+        const float *hb = q + 1 < a.nfields ? a.f.in[q + 1] : ha;  // an odd last field pairs with itself
+        float2 cs = make_float2(0.f, 0.f), ls = cs;
 #pragma unroll
-    for (int kz = 0; kz < 4; ++kz) {
-        float syc[NFM], syl[NFM];
+        for (int kz = 0; kz < 4; ++kz) {
+            float2 syc = make_float2(0.f, 0.f), syl = syc;
 #pragma unroll
-        for (int q = 0; q < NFM; ++q) syc[q] = syl[q] = 0.f;
-#pragma unroll
-        for (int ky = 0; ky < 4; ++ky) {
-            const long long ro = oz[kz] + oy[ky];
-#pragma unroll
-            for (int q = 0; q < NFM; ++q) {
-                if (q >= a.nfields) break;
-                const float *row = a.f.in[q] + ro;
-                float t0, t1, t2, t3;
+            for (int ky = 0; ky < 4; ++ky) {
+                const unsigned ro = oz[kz] + oy[ky];
+                float2 t0, t1, t2, t3;
                 if (XIN) {
-                    row += x0;
-                    t0 = __ldg(row);
-                    t1 = __ldg(row + 1);
-                    t2 = __ldg(row + 2);
-                    t3 = __ldg(row + 3);
+                    const float *ra = ha + ro + x0, *rb = hb + ro + x0;
+                    t0 = make_float2(__ldg(ra), __ldg(rb));
+                    t1 = make_float2(__ldg(ra + 1), __ldg(rb + 1));
+                    t2 = make_float2(__ldg(ra + 2), __ldg(rb + 2));
+                    t3 = make_float2(__ldg(ra + 3), __ldg(rb + 3));
                 } else {
-                    t0 = __ldg(row + ox[0]);
-                    t1 = __ldg(row + ox[1]);
-                    t2 = __ldg(row + ox[2]);
-                    t3 = __ldg(row + ox[3]);
+                    const float *ra = ha + ro, *rb = hb + ro;
+                    t0 = make_float2(__ldg(ra + ox[0]), __ldg(rb + ox[0]));
+                    t1 = make_float2(__ldg(ra + ox[1]), __ldg(rb + ox[1]));
+                    t2 = make_float2(__ldg(ra + ox[2]), __ldg(rb + ox[2]));
+                    t3 = make_float2(__ldg(ra + ox[3]), __ldg(rb + ox[3]));
                 }
-                const float r = fmaf(wc[0][3], t3, fmaf(wc[0][2], t2, fmaf(wc[0][1], t1, wc[0][0] * t0)));
-                syc[q] = fmaf(wc[1][ky], r, syc[q]);
-                if (ky == 1 || ky == 2)
-                    syl[q] = fmaf(ky == 1 ? 1.f - xf[1] : xf[1], fmaf(xf[0], t2, (1.f - xf[0]) * t1), syl[q]);
+                float2 r = __fmul2_rn(w0, t0);
+                r = __ffma2_rn(w1, t1, r);
+                r = __ffma2_rn(w2, t2, r);
+                r = __ffma2_rn(w3, t3, r);
+                syc = __ffma2_rn(make_float2(wc[1][ky], wc[1][ky]), r, syc);
+                if (ky == 1 || ky == 2) {
+                    const float v = ky == 1 ? 1.f - xf[1] : xf[1];
+                    syl = __ffma2_rn(make_float2(v, v), __ffma2_rn(u1, t2, __fmul2_rn(u0, t1)), syl);
+                }
+            }
+            cs = __ffma2_rn(make_float2(wc[2][kz], wc[2][kz]), syc, cs);
+            if (kz == 1 || kz == 2) {
+                const float v = kz == 1 ? 1.f - xf[2] : xf[2];
+                ls = __ffma2_rn(make_float2(v, v), syl, ls);
             }
         }
-#pragma unroll
-        for (int q = 0; q < NFM; ++q) {
-            cub[q] = fmaf(wc[2][kz], syc[q], cub[q]);
-            if (kz == 1 || kz == 2) lin[q] = fmaf(kz == 1 ? 1.f - xf[2] : xf[2], syl[q], lin[q]);
+        cub[q] = cs.x;
+        lin[q] = ls.x;
+        if (q + 1 < NFM) {
+            cub[q + 1] = cs.y;
+            lin[q + 1] = ls.y;
         }
     }
 }
@@ -261,7 +299,17 @@ __global__ void __launch_bounds__(NT3, 3) remap_blocked3d_kernel(const Blocked3A
         bool degen = false;
         int st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters, &degen);
         if (st != ST_OK || degen) {
-            st = resolve3_f64(g, a.D, a.max_iter, a.walk_max, j, c0, st, c, xf, hops, iters);
+            const Resolve3 r = resolve3_f64(a.D, g.n0, g.n1, g.n2, a.max_iter, a.walk_max, j[0], j[1], j[2], st, c[0],
+                                            c[1], c[2], c0[0], c0[1], c0[2]);
+            st = r.st;
+            c[0] = r.c0;
+            c[1] = r.c1;
+            c[2] = r.c2;
+            xf[0] = r.x0;
+            xf[1] = r.x1;
+            xf[2] = r.x2;
+            hops += r.hops;
+            iters += r.iters;
             cnt.f64 += 1;
         }
         cnt.targets = 1;
@@ -281,12 +329,12 @@ __global__ void __launch_bounds__(NT3, 3) remap_blocked3d_kernel(const Blocked3A
             for (int q = 0; q < 3; ++q) cubic_w(xf[q], wc[q]);
             // wrapped node offsets of the stencil c-1 .. c+2 along each axis
             int ox[4];
-            long long oy[4], oz[4];
+            unsigned oy[4], oz[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 ox[k] = wrap3(c[0] - 1 + k, g.n0);
-                oy[k] = (long long)wrap3(c[1] - 1 + k, g.n1) * g.n0;
-                oz[k] = (long long)wrap3(c[2] - 1 + k, g.n2) * g.n0 * g.n1;
+                oy[k] = (unsigned)wrap3(c[1] - 1 + k, g.n1) * (unsigned)g.n0;
+                oz[k] = (unsigned)wrap3(c[2] - 1 + k, g.n2) * (unsigned)g.n0 * (unsigned)g.n1;
             }
             float cub[NFM], lin[NFM];
             if (c[0] >= 1 && c[0] + 2 < g.n0)

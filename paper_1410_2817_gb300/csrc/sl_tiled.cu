@@ -12,7 +12,7 @@ template <typename T>
 bool Launch<T>::tiled_supported(const sl_grid *g)
 {
     if (sizeof(T) != 4 || g->desc.max_order > 1 || g->desc.walk_start != SL_START_BACKWARD) return false;
-    if (g->dim == 3) return true;
+    if (g->dim == 3) return g->N < (1LL << 31);  // the blocked kernel forms 32-bit node offsets
     const int c = g->desc.tile_config;
     const size_t smem = c == 2   ? tiled2d_smem_bytes_cfgb(g->nfields)
                         : c == 3 ? tiled2d_smem_bytes_cfgc(g->nfields)
