@@ -554,10 +554,10 @@ __device__ __forceinline__ void tile_compute(const TileArgs &a, const VelArgs<fl
             unsigned vp = 0u, vc = m[0] | m[nwx] | m[2 * nwx] | m[3 * nwx];
             for (int kw = 0; kw < nwx; ++kw) {
                 const int k1 = kw + 1;
-                const unsigned vn = k1 < nwx ? (m[k1] | m[nwx + k1] | m[2 * nwx + k1] | m[3 * nwx + k1]) : 0u;
-                b[kw] = vc | __funnelshift_l(vp, vc, 1) | __funnelshift_r(vc, vn, 1) | __funnelshift_r(vc, vn, 2);
+                const unsigned vq = k1 < nwx ? (m[k1] | m[nwx + k1] | m[2 * nwx + k1] | m[3 * nwx + k1]) : 0u;
+                b[kw] = vc | __funnelshift_l(vp, vc, 1) | __funnelshift_r(vc, vq, 1) | __funnelshift_r(vc, vq, 2);
                 vp = vc;
-                vc = vn;
+                vc = vq;
             }
         }
         __syncthreads();
@@ -606,11 +606,6 @@ __device__ __forceinline__ void tile_compute(const TileArgs &a, const VelArgs<fl
         } else {
             slow |= 1u << k;
         }
-        if (FUSED && a.D_next != nullptr) {
-            float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
-            rk4_cells<float, 2>(vn, X, d);
-            reinterpret_cast<float2 *>(a.D_next)[jj] = make_float2(d[0], d[1]);
-        }
     }
 #pragma unroll 1
     for (int k = 0; slow != 0u; ++k, slow >>= 1) {
@@ -639,6 +634,22 @@ __device__ __forceinline__ void tile_compute(const TileArgs &a, const VelArgs<fl
     }
 }
 
+
+// eq. (vel): the next step's trajectories of the tile's own nodes (fused steps).  They depend on
+// the velocity only, so callers run them while the window copies are in flight.
+template <class Cfg>
+__device__ __forceinline__ void integrate_next(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0)
+{
+    const int tx = threadIdx.x % Cfg::TX, ty = threadIdx.x / Cfg::TX;
+#pragma unroll 1
+    for (int k = 0; k < Cfg::TPT; ++k) {
+        const int jx = x0 + tx, jy = y0 + ty + k * Cfg::ROWS;
+        if (jx >= a.n0 || jy >= a.n1) continue;
+        float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
+        rk4_cells<float, 2>(vn, X, d);
+        reinterpret_cast<float2 *>(a.D_next)[(long long)jy * a.n0 + jx] = make_float2(d[0], d[1]);
+    }
+}
 
 // One TX x TY tile of targets with origin (x0, y0), staged and computed in one pass: every thread
 // of the CTA calls this; it synchronises the CTA.
@@ -674,6 +685,7 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     // ---- phase 2: stage displacements and fields of the window (all copies in flight) -------
     stage_window<Cfg, NF>(a, w, sm.D, sm.H);
     clear_flags<Cfg, NF>(a, w, sm.M);
+    if (FUSED && a.D_next != nullptr) integrate_next<Cfg>(a, vn, x0, y0);
     cp_async_wait_all();
     __syncthreads();
     tile_compute<Cfg, NF, FUSED>(a, vn, x0, y0, w, staged, sm.D, sm.H, sm.S, sm.M, sm.B, cnt);
@@ -776,6 +788,7 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
                 __syncthreads();
             }
             const int tr = t / tiles_x;
+            if (FUSED && a.D_next != nullptr) integrate_next<Cfg>(a, vn, (t - tr * tiles_x) * TX, tr * TY);
             tile_compute<Cfg, NF, FUSED>(a, vn, (t - tr * tiles_x) * TX, tr * TY, w_cur, st_cur, sD + p * WMAX,
                                          sH + p * NG * WMAX, sS + s3 * NTGT, sM, sB, cnt);
             w_cur = w_nxt;

@@ -127,7 +127,17 @@ def _stream(stream) -> C.c_void_p:
     return C.c_void_p(int(stream))
 
 
-def _planes(ts: Sequence[torch.Tensor]):
+def _planes(ts):
+    """Host array of plane pointers: from a sequence of contiguous CUDA tensors, or from one
+    contiguous CUDA tensor whose leading axis indexes the planes (no per-plane views)."""
+    if isinstance(ts, torch.Tensor):
+        if not ts.is_cuda or not ts.is_contiguous() or ts.dim() < 2:
+            raise ValueError("field planes must be contiguous CUDA tensors")
+        nplanes = ts.shape[0]
+        step = (ts.numel() // max(nplanes, 1)) * ts.element_size()
+        base = ts.data_ptr()
+        arr = (C.c_void_p * nplanes)(*[base + q * step for q in range(nplanes)])
+        return C.cast(arr, C.POINTER(C.c_void_p)), arr
     arr = (C.c_void_p * len(ts))()
     for q, t in enumerate(ts):
         if not t.is_cuda or not t.is_contiguous():
@@ -288,8 +298,16 @@ class Grid:
     def advect(self, t, dt, stream=None):
         sl_advect_nodes(self.handle, t, dt, stream)
 
+    def _fit(self, planes):
+        """The nfields planes of this grid (a stacked tensor or a sequence); others raise."""
+        n = planes.shape[0] if isinstance(planes, torch.Tensor) else len(planes)
+        size = planes[0].numel() if n > 0 else 0
+        if n != self.nfields or size != self.nnodes:
+            raise ValueError(f"expected {self.nfields} planes of {self.nnodes} values")
+        return planes
+
     def remap(self, fin: torch.Tensor, fout: torch.Tensor, stream=None):
-        sl_remap_fields(self.handle, list(fin), list(fout), stream)
+        sl_remap_fields(self.handle, self._fit(fin), self._fit(fout), stream)
 
     def remap_debug(self, fin, fout, stream=None):
         dev = fin.device
@@ -303,7 +321,7 @@ class Grid:
         return cell, xi, order, status
 
     def step(self, fields: torch.Tensor, scratch: torch.Tensor, t0, dt, nsteps, stream=None):
-        sl_step(self.handle, list(fields), list(scratch), t0, dt, nsteps, stream)
+        sl_step(self.handle, self._fit(fields), self._fit(scratch), t0, dt, nsteps, stream)
 
     def moments(self, field: torch.Tensor, pmax=4, stream=None):
         return sl_moments(self.handle, field, pmax, stream)
