@@ -137,9 +137,9 @@ def _max_over_ranks(dist, torch, value: float) -> float:
     return float(t.item())
 
 
-def cpu_baseline(budget_s: float = 20.0, steps_max: int = 4):
-    """The oracle (as it stands) on the GPU machine's host cores: whole 1024^2 steps until the budget
-    is spent (at least one)."""
+def cpu_baseline(budget_s: float = 10.0, steps_max: int = 400):
+    """The oracle (as it stands) on the GPU machine's host cores: whole 1024^2 steps until about
+    `budget_s` seconds of CPU work are spent (at least one step)."""
     from oracle import oracle
     from paper_1410_2817_gb300 import inputs
     wl = inputs.workload_swirl(N_SIDE)

@@ -92,7 +92,7 @@ typedef struct {
     int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
     int walk_start;                 /* SL_START_BACKWARD (from j - D_j) or SL_START_PAPER (Sec. 2.2) */
     int kernel;                     /* SL_KERNEL_AUTO, SL_KERNEL_GENERIC or SL_KERNEL_TILED           */
-    int tile_config;                /* 2-D FP32 tiles: 0 default (= 5), 1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16
+    int tile_config;                /* 2-D FP32 tiles: 0 default (= 1), 1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16
                                        compiled for 4 CTAs per SM, 5: 32x32 pipelined (persistent,
                                        one CTA per SM staging the next tiles while it computes;
                                        1 above 4 fields; batches run 5 as 1)                      */
