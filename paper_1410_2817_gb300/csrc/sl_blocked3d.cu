@@ -6,18 +6,21 @@
 //   * box_flags: the jump flags of Sec. 2.3 are computed once per node and OR-ed over every
 //     element's 4x4x4 stencil [c-1, c+2]^3 (separable: x, then y, then z), so choosing the order
 //     of a target (Sec. 2.3) costs one byte load;
-//   * remap_blocked3d_kernel: one thread per target; a CTA covers an 8x8x4 block of targets so
+//   * remap_blocked3d_kernel: one thread per target; a CTA covers a 16x4x4 block of targets so
 //     that the element search (Sec. 2.2, Newton in FP32 with FP64 re-solves near faces) and the
 //     64-tap tricubic sum (eq. multiZ) of neighbouring targets hit the same L1 lines.  The fused
 //     variant also integrates the next step's trajectories (eq. vel) for its own nodes.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "sl_internal.h"
 
 namespace {
 
-constexpr int BX = 8, BY = 8, BZ = 4, NT3 = BX * BY * BZ;
+constexpr int BX = 16, BY = 4, BZ = 4, NT3 = BX * BY * BZ;
 
 struct Geo3 {
     int n0, n1, n2;
@@ -35,43 +38,89 @@ struct Fields3 {
     float *out[SL_MAX_FIELDS];
 };
 
-// ---- Sec. 2.3 flags and their OR over [c-1, c+2] along one axis -----------------------------
-__global__ void __launch_bounds__(256) flags3d_kernel(Geo3 g, int nfields, float thr, Fields3 f, uint8_t *flags)
+// ---- Sec. 2.3 flags and their OR over each element's stencil [c-1, c+2]^3 ------------------
+// Two passes.  flags_x3d: a warp covers 32 consecutive nodes x0-1 .. x0+30 of one row, tests each
+// node (6 neighbours per field, wrapped) and ORs the flags of x-1 .. x+2 with shuffles, writing
+// the 29 nodes x0 .. x0+28.  box_yz3d: ORs those bytes over y-1 .. y+2 and z-1 .. z+2.  Blocks
+// are 32 x 8 threads over (x, y) and loop over y and z, so no index is divided.
+constexpr int FX = 29;  // nodes written per warp and row by flags_x3d
+
+template <int NFM>
+__global__ void __launch_bounds__(256)
+    flags_x3d_kernel(Geo3 g, int nfields, float thr, Fields3 f, uint8_t *out, int zchunk)
 {
-    const long long N = (long long)g.n0 * g.n1 * g.n2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.n0), y = (int)((i / g.n0) % g.n1), z = (int)(i / ((long long)g.n0 * g.n1));
-        unsigned bits = 0;
-        if (thr >= 0.f) {
-            const long long xm = lin3(g, x - 1, y, z), xp = lin3(g, x + 1, y, z);
-            const long long ym = lin3(g, x, y - 1, z), yp = lin3(g, x, y + 1, z);
-            const long long zm = lin3(g, x, y, z - 1), zp = lin3(g, x, y, z + 1);
-            for (int q = 0; q < nfields; ++q) {
-                const float *h = f.in[q];
-                const float h0 = __ldg(h + i);
-                const bool hit = jump_test<float>(__ldg(h + xm), h0, __ldg(h + xp), thr) ||
-                                 jump_test<float>(__ldg(h + ym), h0, __ldg(h + yp), thr) ||
-                                 jump_test<float>(__ldg(h + zm), h0, __ldg(h + zp), thr);
-                bits |= hit ? (1u << q) : 0u;
+    const int lane = threadIdx.x;
+    const int x0 = blockIdx.x * FX;
+    const int x = wrap_idx(x0 - 1 + lane, g.n0);  // rows shorter than a warp wrap more than once
+    const int xm = wrap_near(x - 1, g.n0), xp = wrap_near(x + 1, g.n0);
+    const long long plane = (long long)g.n0 * g.n1;
+    const int zb = blockIdx.z * zchunk, ze = min(g.n2, zb + zchunk);
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < g.n1; y += gridDim.y * blockDim.y) {
+        const long long yc = (long long)y * g.n0 + x, ym = (long long)wrap_near(y - 1, g.n1) * g.n0 + x,
+                        yp = (long long)wrap_near(y + 1, g.n1) * g.n0 + x;
+        const long long xl = (long long)y * g.n0 + xm, xr = (long long)y * g.n0 + xp;
+        // a thread walks z through its chunk keeping the centre values of planes z-1 and z
+        float cm[NFM], cc[NFM];
+#pragma unroll
+        for (int q = 0; q < NFM; ++q) {
+            cm[q] = cc[q] = 0.f;
+            if (q < nfields) {
+                cm[q] = __ldg(f.in[q] + wrap_near(zb - 1, g.n2) * plane + yc);
+                cc[q] = __ldg(f.in[q] + zb * plane + yc);
             }
         }
-        flags[i] = (uint8_t)bits;
+#pragma unroll 2
+        for (int z = zb; z < ze; ++z) {
+            const long long zc = z * plane, zp = wrap_near(z + 1, g.n2) * plane;
+            unsigned bits = 0;
+#pragma unroll
+            for (int q = 0; q < NFM; ++q) {
+                if (q < nfields) {
+                    const float *h = f.in[q];
+                    const float cp = __ldg(h + zp + yc);
+                    const float l = __ldg(h + zc + xl), r = __ldg(h + zc + xr);
+                    const float d = __ldg(h + zc + ym), u = __ldg(h + zc + yp);
+                    const bool hit = jump_test<float>(l, cc[q], r, thr) | jump_test<float>(d, cc[q], u, thr) |
+                                     jump_test<float>(cm[q], cc[q], cp, thr);
+                    bits |= (hit && thr >= 0.f) ? (1u << q) : 0u;
+                    cm[q] = cc[q];
+                    cc[q] = cp;
+                }
+            }
+            // lane l holds node x0 - 1 + l: the OR over x-1 .. x+2 for l = 1 .. 29
+            const unsigned left = __shfl_up_sync(0xffffffffu, bits, 1);
+            const unsigned r1 = __shfl_down_sync(0xffffffffu, bits, 1);
+            const unsigned r2 = __shfl_down_sync(0xffffffffu, bits, 2);
+            const int xo = x0 - 1 + lane;
+            if (lane >= 1 && lane <= FX && xo < g.n0)
+                out[zc + (long long)y * g.n0 + xo] = (uint8_t)(left | bits | r1 | r2);
+        }
     }
 }
 
-// out[c] = OR of in[c-1 .. c+2] along `axis`
-__global__ void __launch_bounds__(256) box_or_kernel(Geo3 g, int axis, const uint8_t *in, uint8_t *out)
+// OR over y-1 .. y+2 and z-1 .. z+2; W = 4 handles 4 consecutive nodes per thread with 32-bit
+// loads (rows of a multiple of 4 nodes), W = 1 one node with byte loads.
+template <int W>
+__global__ void __launch_bounds__(256) box_yz3d_kernel(Geo3 g, const uint8_t *__restrict__ in, uint8_t *out)
 {
-    const long long N = (long long)g.n0 * g.n1 * g.n2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.n0), y = (int)((i / g.n0) % g.n1), z = (int)(i / ((long long)g.n0 * g.n1));
-        uint8_t r = 0;
+    typedef typename std::conditional<W == 4, unsigned, uint8_t>::type V;
+    const int x = (blockIdx.x * 32 + threadIdx.x) * W;
+    if (x >= g.n0) return;  // no barriers below
+    const long long plane = (long long)g.n0 * g.n1;
+    for (int z = blockIdx.z; z < g.n2; z += gridDim.z) {
+        long long zo[4];
 #pragma unroll
-        for (int o = -1; o <= 2; ++o) {
-            const long long k = axis == 0 ? lin3(g, x + o, y, z) : axis == 1 ? lin3(g, x, y + o, z) : lin3(g, x, y, z + o);
-            r |= in[k];
+        for (int k = 0; k < 4; ++k) zo[k] = wrap_near(z - 1 + k, g.n2) * plane;
+        for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < g.n1; y += gridDim.y * blockDim.y) {
+            V r = 0;
+#pragma unroll
+            for (int ky = 0; ky < 4; ++ky) {
+                const long long yo = (long long)wrap_near(y - 1 + ky, g.n1) * g.n0 + x;
+#pragma unroll
+                for (int kz = 0; kz < 4; ++kz) r |= __ldg(reinterpret_cast<const V *>(in + zo[kz] + yo));
+            }
+            *reinterpret_cast<V *>(out + z * plane + (long long)y * g.n0 + x) = r;
         }
-        out[i] = r;
     }
 }
 
@@ -254,7 +303,7 @@ __device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4],
 }
 
 template <int NFM, bool FUSED>
-__global__ void __launch_bounds__(NT3, 3) remap_blocked3d_kernel(const Blocked3Args a, const VelArgs<float> vn)
+__global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3Args a, const VelArgs<float> vn)
 {
     const Geo3 &g = a.g;
     const int jx = blockIdx.x * BX + threadIdx.x % BX;
@@ -362,19 +411,33 @@ __global__ void __launch_bounds__(NT3, 3) remap_blocked3d_kernel(const Blocked3A
 
 }  // namespace
 
-// box flags of a 3-D FP32 grid into g->flags (uses D[other] as scratch? no: two byte buffers are
-// carved from the flags region and the spare displacement buffer is never touched)
+// box flags of a 3-D FP32 grid: flags ORed along x into `flags`, then over y and z into `tmp`
 cudaError_t launch_box_flags3d(const sl_grid *g, const void *const *in, uint8_t *flags, uint8_t *tmp, cudaStream_t s)
 {
     Geo3 geo = {(int)g->n[0], (int)g->n[1], (int)g->n[2]};
     Fields3 f;
     memset(&f, 0, sizeof(f));
     for (int q = 0; q < g->nfields; ++q) f.in[q] = (const float *)in[q];
-    const int blocks = grid_stride_blocks(g, g->N, 256);
-    flags3d_kernel<<<blocks, 256, 0, s>>>(geo, g->nfields, (float)g->desc.limiter_threshold, f, flags);
-    box_or_kernel<<<blocks, 256, 0, s>>>(geo, 0, flags, tmp);
-    box_or_kernel<<<blocks, 256, 0, s>>>(geo, 1, tmp, flags);
-    box_or_kernel<<<blocks, 256, 0, s>>>(geo, 2, flags, tmp);
+    const dim3 block(32, 8);
+    const unsigned gy = (unsigned)std::min<long long>((g->n[1] + 7) / 8, 65535);
+    const unsigned gz = (unsigned)std::min<long long>(g->n[2], 65535);
+    const int zchunk = (int)std::max<long long>(16, (g->n[2] + 65534) / 65535);
+    const dim3 gridf((unsigned)((g->n[0] + FX - 1) / FX), gy, (unsigned)((g->n[2] + zchunk - 1) / zchunk));
+    const float thr = (float)g->desc.limiter_threshold;
+    if (g->nfields <= 2)
+        flags_x3d_kernel<2><<<gridf, block, 0, s>>>(geo, g->nfields, thr, f, flags, zchunk);
+    else if (g->nfields <= 4)
+        flags_x3d_kernel<4><<<gridf, block, 0, s>>>(geo, g->nfields, thr, f, flags, zchunk);
+    else
+        flags_x3d_kernel<8><<<gridf, block, 0, s>>>(geo, g->nfields, thr, f, flags, zchunk);
+    // the byte buffers start 256-byte aligned; rows of a multiple of 4 nodes keep 32-bit alignment
+    if (g->n[0] % 4 == 0) {
+        const dim3 gridb((unsigned)((g->n[0] / 4 + 31) / 32), gy, gz);
+        box_yz3d_kernel<4><<<gridb, block, 0, s>>>(geo, flags, tmp);
+    } else {
+        const dim3 gridb((unsigned)((g->n[0] + 31) / 32), gy, gz);
+        box_yz3d_kernel<1><<<gridb, block, 0, s>>>(geo, flags, tmp);
+    }
     return cudaGetLastError();
 }
 

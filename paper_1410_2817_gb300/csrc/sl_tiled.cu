@@ -5,8 +5,8 @@
 
 #include "sl_internal.h"
 
-// 2-D: one tiled launch; 3-D: flags + three box-OR passes + one blocked launch
-int tiled_kernels_per_call(const sl_grid *g) { return g->dim == 2 ? 1 : 5; }
+// 2-D: one tiled launch; 3-D: flags with the x-OR, the y/z-OR, one blocked launch
+int tiled_kernels_per_call(const sl_grid *g) { return g->dim == 2 ? 1 : 3; }
 
 template <typename T>
 bool Launch<T>::tiled_supported(const sl_grid *g)
