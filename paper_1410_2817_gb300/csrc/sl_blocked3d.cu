@@ -329,9 +329,29 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             // trilinear over the 8 nodes around s0 (the walk below still decides)
             const float fx = s0[0] - (float)c0[0], fy = s0[1] - (float)c0[1], fz = s0[2] - (float)c0[2];
             float dd[3] = {0.f, 0.f, 0.f};
+            // nodes at fixed offsets from one base when the element does not touch the seam
+            const bool inner = (unsigned)c0[0] < (unsigned)(g.n0 - 1) && (unsigned)c0[1] < (unsigned)(g.n1 - 1) &&
+                               (unsigned)c0[2] < (unsigned)(g.n2 - 1);
+            const long long sy = g.n0, sz = (long long)g.n0 * g.n1;
+            float4 d8[8];
+            if (inner) {
+                const float4 *b = a.D + ((long long)c0[2] * g.n1 + c0[1]) * g.n0 + c0[0];
+                d8[0] = __ldg(b);
+                d8[1] = __ldg(b + 1);
+                d8[2] = __ldg(b + sy);
+                d8[3] = __ldg(b + sy + 1);
+                d8[4] = __ldg(b + sz);
+                d8[5] = __ldg(b + sz + 1);
+                d8[6] = __ldg(b + sz + sy);
+                d8[7] = __ldg(b + sz + sy + 1);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    d8[v] = __ldg(a.D + lin3(g, c0[0] + (v & 1), c0[1] + ((v >> 1) & 1), c0[2] + (v >> 2)));
+            }
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                const float4 d = __ldg(a.D + lin3(g, c0[0] + (v & 1), c0[1] + ((v >> 1) & 1), c0[2] + (v >> 2)));
+                const float4 d = d8[v];
                 const float w = ((v & 1) ? fx : 1.f - fx) * (((v >> 1) & 1) ? fy : 1.f - fy) * ((v >> 2) ? fz : 1.f - fz);
                 dd[0] = fmaf(w, d.x, dd[0]);
                 dd[1] = fmaf(w, d.y, dd[1]);
@@ -372,18 +392,33 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             cnt.ff = st == ST_FOLD;
             for (int q = 0; q < a.nfields; ++q) a.f.out[q][jj] = __ldg(a.f.in[q] + jj);
         } else {
-            const unsigned bits = a.max_order >= 1 ? (unsigned)__ldg(a.box + lin3(g, c[0], c[1], c[2])) : 0xffu;
             float wc[3][4];
 #pragma unroll
             for (int q = 0; q < 3; ++q) cubic_w(xf[q], wc[q]);
-            // wrapped node offsets of the stencil c-1 .. c+2 along each axis
+            // node offsets of the stencil c-1 .. c+2 along each axis: direct when the stencil does
+            // not cross the periodic seam (c in [1, n-3] on every axis), wrapped otherwise
+            const bool inner = (unsigned)(c[0] - 1) < (unsigned)(g.n0 - 3) &&
+                               (unsigned)(c[1] - 1) < (unsigned)(g.n1 - 3) && (unsigned)(c[2] - 1) < (unsigned)(g.n2 - 3);
+            const unsigned sy = (unsigned)g.n0, sz = (unsigned)g.n0 * (unsigned)g.n1;
             int ox[4];
             unsigned oy[4], oz[4];
+            unsigned bits = 0xffu;
+            if (inner) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                ox[k] = wrap3(c[0] - 1 + k, g.n0);
-                oy[k] = (unsigned)wrap3(c[1] - 1 + k, g.n1) * (unsigned)g.n0;
-                oz[k] = (unsigned)wrap3(c[2] - 1 + k, g.n2) * (unsigned)g.n0 * (unsigned)g.n1;
+                for (int k = 0; k < 4; ++k) {
+                    ox[k] = c[0] - 1 + k;
+                    oy[k] = (unsigned)(c[1] - 1 + k) * sy;
+                    oz[k] = (unsigned)(c[2] - 1 + k) * sz;
+                }
+                if (a.max_order >= 1) bits = __ldg(a.box + oz[1] + oy[1] + (unsigned)c[0]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    ox[k] = wrap3(c[0] - 1 + k, g.n0);
+                    oy[k] = (unsigned)wrap3(c[1] - 1 + k, g.n1) * sy;
+                    oz[k] = (unsigned)wrap3(c[2] - 1 + k, g.n2) * sz;
+                }
+                if (a.max_order >= 1) bits = __ldg(a.box + lin3(g, c[0], c[1], c[2]));
             }
             float cub[NFM], lin[NFM];
             if (c[0] >= 1 && c[0] + 2 < g.n0)
