@@ -178,7 +178,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "swirl2d_1024x1024_3fields", "n": N_SIDE, "fields": NFIELDS,
-                                            "cfl": 5, "l2": "not applicable (CPU)"},
+                                            "cfl": 5, "steps_per_call": 1, "newton": "f64 (the oracle)",
+                                            "max_order": 1, "l2": "not applicable (host cores)",
+                                            "parallelism": f"OpenMP x{oracle.max_threads()} on rank 0"},
             "cpu_baseline": {"kind": "oracle", "cores": oracle.max_threads(), "value": value, "unit": UNIT,
                              "sample": f"{args.steps} full steps of the workload (after {args.warmup} warm-up)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
