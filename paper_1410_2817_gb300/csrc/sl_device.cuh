@@ -94,7 +94,33 @@ __device__ __forceinline__ float recip_t(float x)
 __device__ __forceinline__ double recip_t(double x) { return 1.0 / x; }
 
 __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
-__device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
+// FP32 sin(pi x), cos(pi x): x = q/2 + r with q = rint(2x) and |r| <= 1/4 (both exact), the Taylor
+// series of sin(pi r) through r^9 and of cos(pi r) through r^10 (truncation below 2e-9 for
+// |pi r| <= pi/4) by Horner's rule in r^2, then the quadrant q mod 4.  Integers and half-integers
+// give exact zeros (stagnation lines stay at rest).  Valid for |x| < 2^30.
+__device__ __forceinline__ void sincospi_t(float x, float *s, float *c)
+{
+    const float q = rintf(2.f * x);
+    const float r = fmaf(-0.5f, q, x);
+    const float u = r * r;
+    // (-1)^k pi^(2k+1) / (2k+1)!  and  (-1)^k pi^(2k) / (2k)!
+    float sn = r * fmaf(u, fmaf(u, fmaf(u, fmaf(u, 8.214588661e-2f, -5.992645293e-1f), 2.550164040e+0f),
+                                -5.167712780e+0f), 3.141592654e+0f);
+    float cs = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, -2.580689139e-2f, 2.353306304e-1f), -1.335262769e+0f),
+                                4.058712126e+0f), -4.934802201e+0f), 1.f);
+    const int qi = (int)q;
+    if (qi & 1) {
+        const float t = sn;
+        sn = cs;
+        cs = -t;
+    }
+    if (qi & 2) {
+        sn = -sn;
+        cs = -cs;
+    }
+    *s = sn;
+    *c = cs;
+}
 
 template <typename T>
 __device__ __forceinline__ T floor_t(T x);

@@ -158,6 +158,30 @@ def test_advect_parity_f64(sl, orc, kind, dim, n, params, t, dt):
     assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, float(np.abs(ref).max()))
 
 
+@pytest.mark.parametrize("kind,dim,n,params,t,dt", [
+    ("swirl2d", 2, (128, 96), [5.0], 0.37, 5 / 128),
+    ("deform3d", 3, (16, 12, 10), [3.0], 0.8, 0.03),
+    ("fourier2d", 2, (48, 48), inputs.fourier2d_params(np.random.default_rng(1)), 0.0, 0.002),
+    ("fourier3d", 3, (12, 12, 12), inputs.fourier3d_params(np.random.default_rng(2)), 0.0, 0.001),
+])
+def test_advect_f32_trig_accuracy(sl, orc, kind, dim, n, params, t, dt):
+    """FP32 trajectories use the library's own sin(pi x) / cos(pi x) (exact argument reduction,
+    Taylor polynomials, ~1e-7 absolute): against the FP64 oracle every displacement stays within
+    FP32 accuracy -- 2e-6 of the largest for arguments in [0, 1] (swirl, deformation); 1e-5 for the
+    Fourier flows, whose mode arguments 2 k.x reach ~16 and carry their own FP32 rounding (a few
+    ulp of 16, amplified by 2 pi |k| in the velocity) -- and the stagnation nodes of the
+    swirl/deformation flows do not move."""
+    og = _og(orc, dim, n, 1, velocity=kind, params=params)
+    ref = orc.advect(og, t, dt)
+    g = _gpu_grid(sl, dim, n, 1, sl.SL_F32, velocity=kind, params=params)
+    g.advect(t, dt)
+    got = g.get_displacement().double().cpu().numpy()[..., :dim]
+    tol = 1e-5 if kind.startswith("fourier") else 2e-6
+    assert np.max(np.abs(got - ref)) <= tol * float(np.abs(ref).max())
+    if kind in ("swirl2d", "deform3d"):
+        assert np.all(got[ref == 0.0] == 0.0)
+
+
 def test_advect_f32_accuracy(sl, orc):
     og = _og(orc, 2, (256, 256), 1, velocity="swirl2d", params=[5.0])
     ref = orc.advect(og, 0.3, 5 / 256)
