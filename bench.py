@@ -270,11 +270,12 @@ def deform3d_leg(torch, sl, inputs, steps=5):
             "ms_per_step": tot / steps}
 
 
-def serving_leg(njobs, rank=0, world=1, budget_gb=120.0, rate_hz=200.0):
+def serving_leg(njobs, rank=0, world=1, budget_gb=120.0, rate_hz=200.0, policy="sjf", max_active=16):
     """The first `njobs` jobs of the served trace (Poisson arrivals, mean `rate_hz` jobs/s -- 200 for
     the configured trace --, seed 1; 70 % 2-D 64^2-2048^2, 30 % 3-D 32^3-192^3, 1-4 fields, 10-200
     steps, 10 % FP64), served in real time by the continuous-batching server under a 120 GB
-    device-memory budget."""
+    device-memory budget; admission shortest-estimated-work first with at most 16 jobs resident
+    ("sjf"), or in arrival order without a cap ("fifo", 4096)."""
     from paper_1410_2817_gb300 import inputs, serve
     jobs = serve.shard_jobs(inputs.serving_trace(njobs=njobs, seed=1, rate_hz=rate_hz), rank, world)  # independent
 
@@ -282,7 +283,8 @@ def serving_leg(njobs, rank=0, world=1, budget_gb=120.0, rate_hz=200.0):
         wl = job.workload
         return inputs.job_fields_device(wl.dim, wl.n[0], wl.nfields, seed=1000 + job.job_id)
 
-    out = serve.serve_trace(jobs, fields_of, budget_bytes=int(budget_gb * (1 << 30)))
+    out = serve.serve_trace(jobs, fields_of, budget_bytes=int(budget_gb * (1 << 30)), policy=policy,
+                            max_active=max_active)
     out.pop("results", None)
     out["trace"] = f"first {njobs} jobs of serving_trace(seed=1, rate_hz={rate_hz:g})"
     return out
@@ -466,6 +468,10 @@ def main():
     # device sustains shows the service latency
     serving_light = (serving_leg(max(args.serve_jobs // 3, 1), rank, ws, rate_hz=12.0)
                      if (not args.no_extra and args.serve_jobs > 0) else None)
+    # the same overloaded trace admitted in arrival order without a cap: every job shares the device
+    # until the end (context for the policy's effect; same throughput)
+    serving_fifo = (serving_leg(args.serve_jobs, rank, ws, policy="fifo", max_active=4096)
+                    if (not args.no_extra and args.serve_jobs > 0) else None)
 
     if rank != 0:
         if dist is not None:
@@ -498,6 +504,7 @@ def main():
         "deform3d_256": deform3d,
         "serving": serving,
         "serving_sustained_rate": serving_light,
+        "serving_fifo_uncapped": serving_fifo,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": plane_bytes, "d2h_bytes_per_step": plane_bytes,
                 "how": "each step: pinned host -> device copy, sl_step, device -> pinned host copy; steps alternate "
                        "between two grids on two streams so copies overlap kernels"},

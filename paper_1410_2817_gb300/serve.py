@@ -12,8 +12,9 @@ advances ALL active jobs by one step per iteration:
 Each of these lanes is relaunched as soon as its previous step has finished (an event per lane,
 polled by the host loop): slow FP64 jobs never hold back the FP32 batches.  Arrived jobs are
 admitted in arrival order while the device-memory budget and the slot limit allow (a job's bytes:
-its grid workspace plus its field and scratch planes), join their lane at its next step, and are
-read back and released when done.  A job's result does not depend on what it is batched with:
+its grid workspace plus its field and scratch planes) -- or, with policy "sjf", shortest
+estimated device work first under a cap on concurrent jobs --, join their lane at its next step,
+and are read back and released when done.  A job's result does not depend on what it is batched with:
 every tile of a batch runs the same code as the job alone.
 
 `Scheduler` holds the queue/admission/budget logic (no GPU); `GpuExecutor` runs jobs through the C
@@ -45,12 +46,20 @@ class JobState:
 
 
 class Scheduler:
-    """FIFO admission under a byte budget and a slot limit."""
+    """Admission under a byte budget and a slot limit.  policy "fifo": in arrival order; "sjf":
+    the queued job with the least estimated device work first (`work_of`, ties by arrival), which
+    under overload lets short jobs finish instead of every job sharing the device until the end.
+    Either way a job that does not fit the budget waits for memory (it is never skipped)."""
 
-    def __init__(self, budget_bytes: int, max_active: int = 4096, bytes_of: Callable[[object], int] = None):
+    def __init__(self, budget_bytes: int, max_active: int = 4096, bytes_of: Callable[[object], int] = None,
+                 policy: str = "fifo", work_of: Callable[[object], float] = None):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError(f"unknown policy {policy!r}")
         self.budget = int(budget_bytes)
         self.max_active = int(max_active)
         self.bytes_of = bytes_of
+        self.policy = policy
+        self.work_of = work_of or (lambda job: float(job.workload.nnodes * job.workload.steps))
         self.queue: collections.deque = collections.deque()
         self.active: Dict[int, JobState] = {}
         self.done: Dict[int, JobState] = {}
@@ -67,10 +76,20 @@ class Scheduler:
             self.queue.append(st)
         return st
 
+    def _next(self) -> Optional[JobState]:
+        if not self.queue:
+            return None
+        if self.policy == "fifo":
+            return self.queue[0]
+        return min(self.queue, key=lambda st: (self.work_of(st.job), st.job.arrival_s, st.job.job_id))
+
     def admit(self, now: float) -> List[JobState]:
         out = []
-        while self.queue and len(self.active) < self.max_active and self.used + self.queue[0].nbytes <= self.budget:
-            st = self.queue.popleft()
+        while len(self.active) < self.max_active:
+            st = self._next()
+            if st is None or self.used + st.nbytes > self.budget:
+                break
+            self.queue.remove(st)
             st.admitted_s = now
             self.active[st.job.job_id] = st
             self.used += st.nbytes
@@ -154,6 +173,18 @@ class GpuExecutor:
                          velocity_params=list(wl.velocity_params), tile_config=self.tile_config)
         tsize = 8 if job.dtype == "f64" else 4
         return sl.sl_grid_workspace_bytes(d) + 2 * wl.nfields * wl.nnodes * tsize
+
+    def work_of(self, job) -> float:
+        """Relative device time of a job: node-steps, weighted by the measured cost of an FP64
+        node-step against an FP32 one (~25x in 2-D, ~30x in 3-D on GB300) and of a 3-D FP32
+        node-step against a 2-D one (~1.6x)."""
+        wl = job.workload
+        w = float(wl.nnodes * wl.steps)
+        if wl.dim == 3:
+            w *= 1.6
+        if job.dtype == "f64":
+            w *= 25.0 if wl.dim == 2 else 30.0
+        return w
 
     def _lane_key(self, st: JobState):
         wl = st.job.workload
@@ -259,11 +290,11 @@ class GpuExecutor:
 
 def serve_trace(jobs: Sequence, fields_of: Callable[[object], np.ndarray], budget_bytes: int,
                 max_active: int = 4096, executor: Optional[GpuExecutor] = None, keep_results: bool = False,
-                poll_sleep_s: float = 5e-5) -> Dict:
+                poll_sleep_s: float = 5e-5, policy: str = "fifo") -> Dict:
     """Serve a trace of inputs.Job in real time (arrival times in seconds from the start).  Returns
     latency percentiles (finish - arrival), throughput, and optionally each job's final fields."""
     ex = executor or GpuExecutor()
-    sched = Scheduler(budget_bytes, max_active, ex.bytes_of)
+    sched = Scheduler(budget_bytes, max_active, ex.bytes_of, policy=policy, work_of=ex.work_of)
     pending = collections.deque(sorted(jobs, key=lambda j: j.arrival_s))
     results = {}
     t_start = time.perf_counter()
@@ -302,5 +333,6 @@ def serve_trace(jobs: Sequence, fields_of: Callable[[object], np.ndarray], budge
         "achieved_node_updates_per_s": total / makespan if makespan > 0 else None,
         "offered_node_updates_per_s": offered / last_arrival if last_arrival > 0 else None,
         "peak_active": sched.peak_active, "peak_bytes": sched.peak_used, "budget_bytes": budget_bytes,
+        "policy": policy, "max_active": max_active,
         "results": results if keep_results else None,
     }

@@ -31,11 +31,13 @@ def _fields_of(job):
     return inputs.job_fields_device(wl.dim, wl.n[0], wl.nfields, seed=1000 + job.job_id)
 
 
-def test_mix_equals_alone(serve):
+@pytest.mark.parametrize("policy,max_active", [("fifo", 4096), ("sjf", 4)])
+def test_mix_equals_alone(serve, policy, max_active):
     jobs = _trace()
     kinds = {(j.workload.dim, j.dtype) for j in jobs}
     assert (2, "f32") in kinds and (3, "f32") in kinds and any(d == "f64" for _, d in kinds)
-    mix = serve.serve_trace(jobs, _fields_of, budget_bytes=8 << 30, keep_results=True)
+    mix = serve.serve_trace(jobs, _fields_of, budget_bytes=8 << 30, keep_results=True, policy=policy,
+                            max_active=max_active)
     assert mix["completed"] == len(jobs) and mix["rejected"] == 0
     assert mix["peak_active"] >= 2  # arrivals overlapped with running jobs
     for job in jobs:

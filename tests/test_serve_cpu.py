@@ -1,5 +1,6 @@
-"""Host-side logic of the server: admission under a budget and a slot limit, FIFO order, release,
-rejection of jobs larger than the budget, and sharding of jobs across ranks (no GPU)."""
+"""Host-side logic of the server: admission under a budget and a slot limit, FIFO and
+shortest-work-first order, release, rejection of jobs larger than the budget, and sharding of jobs
+across ranks (no GPU)."""
 import numpy as np
 
 from paper_1410_2817_gb300 import inputs
@@ -44,6 +45,46 @@ def test_oversized_job_is_rejected_not_blocking():
     assert sch.done[1].rejected
     got = [s.job.job_id for s in sch.admit(0.0)]
     assert got == [0, 2]  # budget 100 holds two 50-byte jobs; the oversized job left the queue
+
+
+def test_sjf_admits_least_work_first_under_the_cap():
+    jobs = _jobs(12)
+    work = {j.job_id: float((7 * j.job_id) % 12) for j in jobs}  # a permutation of 0..11
+    sch = Scheduler(budget_bytes=10 ** 9, max_active=4, bytes_of=lambda j: 100, policy="sjf",
+                    work_of=lambda j: work[j.job_id])
+    for j in jobs:
+        sch.submit(j)
+    first = [s.job.job_id for s in sch.admit(0.0)]
+    assert sorted(work[i] for i in first) == [0.0, 1.0, 2.0, 3.0] and len(sch.active) == 4
+    order = list(first)
+    t = 0.1
+    while not sch.idle():
+        st = min(sch.active.values(), key=lambda s: s.job.job_id)
+        sch.finish(st, t)
+        order += [s.job.job_id for s in sch.admit(t)]
+        assert len(sch.active) <= 4
+        t += 0.1
+    assert [work[i] for i in order] == sorted(work.values())  # admitted in increasing work
+
+
+def test_sjf_waits_for_memory_instead_of_skipping():
+    jobs = _jobs(3)
+    size = {0: 80, 1: 60, 2: 10}
+    work = {0: 3.0, 1: 1.0, 2: 2.0}
+    sch = Scheduler(budget_bytes=100, max_active=8, bytes_of=lambda j: size[j.job_id], policy="sjf",
+                    work_of=lambda j: work[j.job_id])
+    for j in jobs:
+        sch.submit(j)
+    assert [s.job.job_id for s in sch.admit(0.0)] == [1, 2]  # 60 + 10; job 0 (80) must wait
+    assert [s.job.job_id for s in sch.admit(0.1)] == []
+    sch.finish(sch.active[1], 0.2)
+    assert [s.job.job_id for s in sch.admit(0.2)] == [0]
+
+
+def test_unknown_policy_rejected():
+    import pytest
+    with pytest.raises(ValueError):
+        Scheduler(budget_bytes=1, policy="lifo", bytes_of=lambda j: 1)
 
 
 def test_percentiles():
