@@ -309,11 +309,26 @@ __global__ void __launch_bounds__(256)
             continue;
         }
         if (dbg.cell) dbg.cell[jj] = node_index<DIM>(c, g.n);
+        // wrapped node offsets of the cubic stencil c-1 .. c+2 along each axis (taps and flags)
+        long long ox[4], oy[4], oz[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ox[k] = wrap_idx(c[0] - 1 + k, g.n[0]);
+            oy[k] = (long long)wrap_idx(c[1] - 1 + k, g.n[1]) * g.n[0];
+            oz[k] = DIM == 3 ? (long long)wrap_idx(c[2] - 1 + k, g.n[2]) * g.n[0] * g.n[1] : 0;
+        }
+        constexpr int KZ = DIM == 3 ? 4 : 1;
         // Sec. 2.3: OR of the flag bytes over the stencils of order 2 ([c-2, c+3]) and 1 ([c-1, c+2])
         unsigned box2 = 0, box1 = 0;
-        if (g.max_order >= 1) {
-            const int r = g.max_order >= 2 ? 2 : 1;
-            const int w = 2 * r + 2;
+        if (g.max_order == 1) {
+#pragma unroll
+            for (int kz = 0; kz < KZ; ++kz)
+#pragma unroll
+                for (int ky = 0; ky < 4; ++ky)
+#pragma unroll
+                    for (int kx = 0; kx < 4; ++kx) box1 |= __ldg(flags + oz[kz] + oy[ky] + ox[kx]);
+        } else if (g.max_order >= 2) {
+            const int r = 2, w = 6;
             const int cnt_box = DIM == 3 ? w * w * w : w * w;
             for (int q = 0; q < cnt_box; ++q) {
                 int o[3] = {q % w - r, (q / w) % w - r, DIM == 3 ? q / (w * w) - r : 0};
@@ -326,6 +341,19 @@ __global__ void __launch_bounds__(256)
                 if (inner) box1 |= fb;
             }
         }
+        // eq. (multiZ) weights of orders 1 (Z~1 at taps c-1 .. c+2, Appendix) and 0 (hat at c, c+1),
+        // once per target
+        T wc[3][4], wl[3][2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T x = a < DIM ? xi[a] : T(0), y = T(1) - x, x2 = x * x, y2 = y * y;
+            wc[a][0] = T(-0.5) * x * y2;
+            wc[a][1] = T(1) + x2 * (T(1.5) * x - T(2.5));
+            wc[a][2] = T(1) + y2 * (T(1.5) * y - T(2.5));
+            wc[a][3] = T(-0.5) * x2 * y;
+            wl[a][0] = y;
+            wl[a][1] = x;
+        }
         for (int q = 0; q < g.nfields; ++q) {
             int m = g.max_order;
             if (m == 2 && ((box2 >> q) & 1u)) m = 1;
@@ -334,20 +362,47 @@ __global__ void __launch_bounds__(256)
             cnt.oh1 += m == 1;
             cnt.oh2 += m == 2;
             if (dbg.order) dbg.order[(long long)q * g.N + jj] = (uint8_t)m;
-            T w[3][6];
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) zs_weights<T>(m, xi[a], w[a]);
-            const int wn = 2 * m + 2;
             const T *h = f.in[q];
             T sum = T(0);
-            const int wz = DIM == 3 ? wn : 1;
-            for (int kz = 0; kz < wz; ++kz) {
-                for (int ky = 0; ky < wn; ++ky) {
-                    for (int kx = 0; kx < wn; ++kx) {
-                        int k[3] = {c[0] - m + kx, c[1] - m + ky, DIM == 3 ? c[2] - m + kz : 0};
-                        T wt = w[0][kx] * w[1][ky];
-                        if (DIM == 3) wt *= w[2][kz];
-                        sum += __ldg(h + node_index<DIM>(k, g.n)) * wt;
+            if (m == 1) {
+#pragma unroll
+                for (int kz = 0; kz < KZ; ++kz) {
+                    T sy = T(0);
+#pragma unroll
+                    for (int ky = 0; ky < 4; ++ky) {
+                        const T *row = h + oz[kz] + oy[ky];
+                        T sx = T(0);
+#pragma unroll
+                        for (int kx = 0; kx < 4; ++kx) sx += wc[0][kx] * __ldg(row + ox[kx]);
+                        sy += wc[1][ky] * sx;
+                    }
+                    sum += (DIM == 3 ? wc[2][kz] : T(1)) * sy;
+                }
+            } else if (m == 0) {
+#pragma unroll
+                for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz) {
+                    T sy = T(0);
+#pragma unroll
+                    for (int ky = 0; ky < 2; ++ky) {
+                        const T *row = h + oz[kz + 1] + oy[ky + 1];
+                        sy += wl[1][ky] * (wl[0][0] * __ldg(row + ox[1]) + wl[0][1] * __ldg(row + ox[2]));
+                    }
+                    sum += (DIM == 3 ? wl[2][kz] : T(1)) * sy;
+                }
+            } else {
+                T w[3][6];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) zs_weights<T>(m, xi[a], w[a]);
+                const int wn = 2 * m + 2;
+                const int wz = DIM == 3 ? wn : 1;
+                for (int kz = 0; kz < wz; ++kz) {
+                    for (int ky = 0; ky < wn; ++ky) {
+                        for (int kx = 0; kx < wn; ++kx) {
+                            int k[3] = {c[0] - m + kx, c[1] - m + ky, DIM == 3 ? c[2] - m + kz : 0};
+                            T wt = w[0][kx] * w[1][ky];
+                            if (DIM == 3) wt *= w[2][kz];
+                            sum += __ldg(h + node_index<DIM>(k, g.n)) * wt;
+                        }
                     }
                 }
             }
