@@ -342,11 +342,9 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
         }
     }
     if (nsteps % 2 == 1) {
-        const size_t bytes = (size_t)g->N * g->tsize;
-        for (int q = 0; q < g->nfields; ++q) {
-            e = cudaMemcpyAsync(fields[q], cur[q], bytes, cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) return e;
-        }
+        // the result sits in the scratch planes: copy every plane back in one launch
+        e = counted(g, Launch<T>::copy_planes(g, cur, fields, s), 1);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

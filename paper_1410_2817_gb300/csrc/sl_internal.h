@@ -47,6 +47,7 @@ struct Launch {
     static cudaError_t remap_generic(const sl_grid *g, const void *D, const uint8_t *flags, const void *const *in,
                                      void *const *out, const sl_remap_debug *dbg, cudaStream_t s);
     static cudaError_t moments(const sl_grid *g, const void *field, int pmax, cudaStream_t s);
+    static cudaError_t copy_planes(const sl_grid *g, const void *const *src, void *const *dst, cudaStream_t s);
     static cudaError_t copy_disp(const sl_grid *g, const void *src, int64_t src_stride, void *dst,
                                  int64_t dst_stride, cudaStream_t s);
     // tiled / fused kernels (sl_tiled.cu)

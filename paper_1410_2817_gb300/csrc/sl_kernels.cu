@@ -9,8 +9,10 @@
 //                         eq. (multiZ) tensor Z-spline sum
 //   moments_*             Sec. 3.1 discrete moments, FP64 accumulation in a fixed order
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "sl_internal.h"
@@ -468,6 +470,25 @@ __global__ void moments_final_kernel(const double *partials, int nblocks, int pm
 // ------------------------------------------------------------------------------------------------
 // strided copy of displacements (set / get)
 // ------------------------------------------------------------------------------------------------
+// every field plane in one launch: 16-byte vector copies when all planes are 16-byte aligned
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(256) copy_planes_kernel(long long N, int nf, FieldPtrs<T> f)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (VEC) {
+        const long long nv = N * (long long)sizeof(T) / 16;
+        for (int q = 0; q < nf; ++q) {
+            const float4 *src = reinterpret_cast<const float4 *>(f.in[q]);
+            float4 *dst = reinterpret_cast<float4 *>(f.out[q]);
+            for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += stride) dst[i] = src[i];
+        }
+    } else {
+        for (int q = 0; q < nf; ++q)
+            for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride)
+                f.out[q][i] = f.in[q][i];
+    }
+}
+
 template <typename T>
 __global__ void copy_disp_kernel(long long N, int dim, const T *__restrict__ src, long long ss, T *__restrict__ dst,
                                  long long dsd)
@@ -567,6 +588,26 @@ cudaError_t Launch<T>::moments(const sl_grid *g, const void *field, int pmax, cu
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     moments_final_kernel<<<1, 32, 0, s>>>(g->partials, SL_MOMENT_BLOCKS, pmax, g->moment_out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::copy_planes(const sl_grid *g, const void *const *src, void *const *dst, cudaStream_t s)
+{
+    FieldPtrs<T> f;
+    memset(&f, 0, sizeof(f));
+    bool vec = ((size_t)g->N * sizeof(T)) % 16 == 0;
+    for (int q = 0; q < g->nfields; ++q) {
+        f.in[q] = (const T *)src[q];
+        f.out[q] = (T *)dst[q];
+        vec = vec && ((uintptr_t)src[q] & 15u) == 0 && ((uintptr_t)dst[q] & 15u) == 0;
+    }
+    const long long work = vec ? (long long)g->N * (long long)sizeof(T) / 16 : (long long)g->N;
+    const int blocks = (int)std::min<long long>(grid_stride_blocks(g, work, 256), (long long)g->num_sms * 8);
+    if (vec)
+        copy_planes_kernel<T, true><<<blocks, 256, 0, s>>>((long long)g->N, g->nfields, f);
+    else
+        copy_planes_kernel<T, false><<<blocks, 256, 0, s>>>((long long)g->N, g->nfields, f);
     return cudaGetLastError();
 }
 
