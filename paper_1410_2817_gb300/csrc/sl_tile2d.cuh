@@ -497,8 +497,8 @@ __device__ __forceinline__ void clear_flags(const TileArgs &a, const Win &w, uns
 
 // Phases 3 and 4 of one tile whose window (sD, sH) and start points (sS) are in shared memory and
 // whose flag plane M is clear: every thread of the CTA calls this; it synchronises the CTA.
-template <class Cfg, int NF, bool FUSED>
-__device__ __forceinline__ void tile_compute(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0, const Win &w,
+template <class Cfg, int NF>
+__device__ __forceinline__ void tile_compute(const TileArgs &a, int x0, int y0, const Win &w,
                                              bool staged, const float2 *sD, const float4 *sH, const float2 *sS,
                                              unsigned *sM, unsigned *sB, LocalCounters &cnt)
 {
@@ -688,7 +688,7 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     if (FUSED && a.D_next != nullptr) integrate_next<Cfg>(a, vn, x0, y0);
     cp_async_wait_all();
     __syncthreads();
-    tile_compute<Cfg, NF, FUSED>(a, vn, x0, y0, w, staged, sm.D, sm.H, sm.S, sm.M, sm.B, cnt);
+    tile_compute<Cfg, NF>(a, x0, y0, w, staged, sm.D, sm.H, sm.S, sm.M, sm.B, cnt);
 }
 
 template <class Cfg, int NF, bool FUSED>
@@ -789,8 +789,8 @@ __global__ void __launch_bounds__(Cfg::NT, 1)
             }
             const int tr = t / tiles_x;
             if (FUSED && a.D_next != nullptr) integrate_next<Cfg>(a, vn, (t - tr * tiles_x) * TX, tr * TY);
-            tile_compute<Cfg, NF, FUSED>(a, vn, (t - tr * tiles_x) * TX, tr * TY, w_cur, st_cur, sD + p * WMAX,
-                                         sH + p * NG * WMAX, sS + s3 * NTGT, sM, sB, cnt);
+            tile_compute<Cfg, NF>(a, (t - tr * tiles_x) * TX, tr * TY, w_cur, st_cur, sD + p * WMAX,
+                                  sH + p * NG * WMAX, sS + s3 * NTGT, sM, sB, cnt);
             w_cur = w_nxt;
             st_cur = st_nxt;
             s3 = s3n;
