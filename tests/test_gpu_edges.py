@@ -1,6 +1,7 @@
 """Edge cases of the CUDA path through the C ABI: the largest and the smallest grid sides, targets
 that all sit on vertices (zero and integer displacements: the remap must return the shifted input
-exactly), one field and eight fields (the widest field groups of the tiled kernels)."""
+exactly), one to eight fields (the field groups of the tiled and blocked kernels), and the
+pipelined tile configuration against the default one."""
 import numpy as np
 import pytest
 import torch
@@ -150,3 +151,42 @@ def test_field_counts_tiled_vs_generic(sl, nf, tile_config):
     # same elements and orders away from faces; a target within the FP32 slack of a face may be
     # taken in the neighbouring element, whose order can differ: such ties stay rare
     assert float((diff > 2e-6 * scale).mean()) <= 2e-4, float(diff.max())
+
+
+def test_pipelined_step_equals_default_tiles(sl):
+    """sl_step on the pipelined configuration (5: persistent CTAs staging the next tiles; the next
+    step's trajectories integrated in the same launch) gives bit-for-bit what the default 32x32
+    configuration gives: the per-target arithmetic is the same code."""
+    wl = inputs.workload_swirl(640, steps=4)  # 20 x 20 tiles: several tiles per CTA on 152 SMs
+    outs = {}
+    for cfg in (1, 5):
+        g = sl.grid_for(wl, sl.SL_F32, tile_config=cfg)
+        f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
+        g.step(f, torch.empty_like(f), 0.1, wl.dt, 4)
+        torch.cuda.synchronize()
+        outs[cfg] = f.cpu()
+        d = g.diagnostics()
+        assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
+    assert torch.equal(outs[1], outs[5])
+
+
+@pytest.mark.parametrize("nf", [3, 6])
+def test_blocked3d_field_counts(sl, nf):
+    """3-D blocked kernel with four-field (three used) and eight-field (six used) register groups:
+    the same values as the plain FP32 kernel."""
+    n = (20, 14, 12)
+    D = inputs.smooth_displacement(n, amplitude=0.3, seed=14, shift=(1.3, -0.8, 2.1))
+    h = _smooth_fields((12, 14, 20), nf, seed=15)
+    h[0] += (np.arange(20)[None, None, :] > 9) * 1.0
+    outs = {}
+    for name, kern in (("generic", sl.SL_KERNEL_GENERIC), ("tiled", sl.SL_KERNEL_TILED)):
+        g = _grid(sl, 3, n, nf, sl.SL_F32, kernel=kern)
+        g.set_displacement(torch.tensor(D, dtype=torch.float32, device=DEV))
+        hin = torch.tensor(h, dtype=torch.float32, device=DEV)
+        hout = torch.empty_like(hin)
+        g.remap(hin, hout)
+        torch.cuda.synchronize()
+        outs[name] = (hout.double().cpu().numpy(), g.diagnostics())
+    diff = np.abs(outs["tiled"][0] - outs["generic"][0])
+    assert float(diff.max()) <= 4e-6 * max(1.0, float(np.abs(h).max())), float(diff.max())
+    assert outs["tiled"][1]["order_hist"] == outs["generic"][1]["order_hist"]
