@@ -140,9 +140,14 @@ def _max_over_ranks(dist, torch, value: float) -> float:
 
 def cpu_baseline(budget_s: float = 10.0, steps_max: int = 400):
     """The oracle (as it stands) on the GPU machine's host cores: whole 1024^2 steps until about
-    `budget_s` seconds of CPU work are spent (at least one step)."""
+    `budget_s` seconds of CPU work are spent (at least one step).  Its result also serves as the
+    reference of the FP32 production path's accuracy: the same number of FP32 steps from the same
+    fields through sl_step, compared field by field (relative L1 and Linf) and in the moments
+    m_0..m_2 (Sec. 3.1)."""
+    import numpy as np
+    import torch
     from oracle import oracle
-    from paper_1410_2817_gb300 import inputs
+    from paper_1410_2817_gb300 import inputs, sl
     wl = inputs.workload_swirl(N_SIDE)
     og = oracle.OracleGrid(dim=2, n=wl.n, nfields=NFIELDS, velocity=wl.velocity, velocity_params=wl.velocity_params)
     h = wl.fields
@@ -153,9 +158,24 @@ def cpu_baseline(budget_s: float = 10.0, steps_max: int = 400):
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    g.step(f, torch.empty_like(f), 0.0, wl.dt, done)
+    got = f.double().cpu().numpy()
+    g.close()
+    names = ("gaussian (smooth)", "step (jump)", "sine (smooth)")
+    acc = {}
+    for q in range(NFIELDS):
+        d = np.abs(got[q] - h[q])
+        mr, mg = oracle.moments(og, h[q], 2), oracle.moments(og, got[q], 2)
+        scale = max(abs(float(oracle.moments(og, np.abs(h[q]), 0)[0])), 1e-300)  # L1 mass of the field
+        acc[names[q]] = {"l1_rel": float(d.sum() / np.abs(h[q]).sum()), "linf_rel": float(d.max() / np.abs(h[q]).max()),
+                         "moments_rel": [float(abs(a - b) / scale) for a, b in zip(mg, mr)]}
     return {"value": wl.nnodes * done / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{done} full step(s) of the 1024^2 x 3-field swirl workload, FP64, OpenMP over targets",
-            "seconds": el}
+            "seconds": el,
+            "fp32_accuracy_vs_oracle": {"steps": done, "fields": acc,
+                                        "note": "moments m_0..m_2 relative to the field's L1 mass"}}
 
 
 def run_reference(args):
