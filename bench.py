@@ -290,6 +290,110 @@ def deform3d_leg(torch, sl, inputs, steps=5):
             "ms_per_step": tot / steps}
 
 
+def integrators_leg(torch, sl, inputs, flush, steps=10):
+    """The headline workload (swirl 1024^2, 3 fields, FP32, L2 flushed before each step) with
+    Williamson's low-storage RK3 in place of RK4, and with the grid moved for four RK3 steps of the
+    headline dt between remaps (one sl_step of 4 dt with four trajectory sub-steps)."""
+    wl = inputs.workload_swirl(N_SIDE)
+    out = {}
+    for name, integ, k in (("wrk3", "wrk3", 1), ("wrk3_remap_every_4", "wrk3", 4), ("rk4_remap_every_4", "rk4", 4)):
+        g = sl.grid_for(wl, sl.SL_F32, integrator=integ, trajectory_substeps=k)
+        f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+        s = torch.empty_like(f)
+        dt = k * wl.dt
+        t = 0.0
+        for _ in range(3):
+            g.step(f, s, t, dt, 1)
+            t += dt
+        ev = []
+        for q in range(steps):
+            flush.fill_(q & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.step(f, s, t, dt, 1)
+            b.record()
+            ev.append((a, b))
+            t += dt
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        d = g.diagnostics()
+        out[name] = {"integrator": integ, "trajectory_substeps": k, "dt": dt, "ms_per_step": ms,
+                     "value": wl.nnodes / (ms * 1e-3), "unit": UNIT,
+                     "integrator_steps_per_s": wl.nnodes * k / (ms * 1e-3),
+                     "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"],
+                     "mean_hops": d["hops_sum"] / max(1, d["targets"])}
+        g.close()
+    return out
+
+
+def quintic_leg(torch, sl, inputs, flush, steps=10):
+    """The headline workload with the quintic Z2 (six points per axis, orders 2 -> 1 -> 0 near
+    jumps): FP32 on the plain kernels (flags, RK4, remap: three launches per step), L2 flushed
+    before each step."""
+    wl = inputs.workload_swirl(N_SIDE)
+    wl.max_order = 2
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    s = torch.empty_like(f)
+    t = 0.0
+    for _ in range(3):
+        g.step(f, s, t, wl.dt, 1)
+        t += wl.dt
+    l0 = g.diagnostics()["kernel_launches"]
+    ev = []
+    for q in range(steps):
+        flush.fill_(q & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(f, s, t, wl.dt, 1)
+        b.record()
+        ev.append((a, b))
+        t += wl.dt
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    d = g.diagnostics()
+    out = {"workload": f"swirl2d {N_SIDE}^2 x 3 fields, Z2, FP32 plain kernels", "ms_per_step": ms,
+           "value": wl.nnodes / (ms * 1e-3), "unit": UNIT, "launches_per_step": (d["kernel_launches"] - l0) / steps,
+           "order_hist": d["order_hist"],
+           "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"]}
+    g.close()
+    return out
+
+
+def burgers_leg(torch, sl, inputs, flush, steps=10):
+    """2-D inviscid Burgers (Sec. 3.2) on 1024^2, FP32: the two velocity components are the
+    transported fields and every node moves with the velocity it carries (dt = dx / 2).  Each
+    step is a trajectory launch (D = dt u / dx) and the tiled remap; L2 flushed before each step.
+    The timed steps start at t = 0.2, after the shock has formed."""
+    wl = inputs.workload_burgers(N_SIDE)
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    s = torch.empty_like(f)
+    warm = int(round(0.2 / wl.dt))
+    g.step(f, s, 0.0, wl.dt, warm)
+    t = warm * wl.dt
+    l0 = g.diagnostics()["kernel_launches"]
+    ev = []
+    for q in range(steps):
+        flush.fill_(q & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(f, s, t, wl.dt, 1)
+        b.record()
+        ev.append((a, b))
+        t += wl.dt
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    d = g.diagnostics()
+    out = {"workload": f"burgers2d {N_SIDE}^2, 2 fields (u, v), FP32, CFL 0.5, timed from t = 0.2",
+           "ms_per_step": ms, "value": wl.nnodes / (ms * 1e-3), "unit": UNIT,
+           "launches_per_step": (d["kernel_launches"] - l0) / steps,
+           "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"],
+           "order_hist": d["order_hist"]}
+    g.close()
+    return out
+
+
 def serving_leg(njobs, rank=0, world=1, budget_gb=120.0, rate_hz=200.0, policy="sjf", max_active=16):
     """The first `njobs` jobs of the served trace (Poisson arrivals, mean `rate_hz` jobs/s -- 200 for
     the configured trace --, seed 1; 70 % 2-D 64^2-2048^2, 30 % 3-D 32^3-192^3, 1-4 fields, 10-200
@@ -486,6 +590,9 @@ def main():
 
     batched = batched_leg(torch, sl, inputs) if not args.no_extra else None
     deform3d = deform3d_leg(torch, sl, inputs) if not args.no_extra else None
+    integrators = integrators_leg(torch, sl, inputs, flush) if not args.no_extra else None
+    burgers = burgers_leg(torch, sl, inputs, flush) if not args.no_extra else None
+    quintic = quintic_leg(torch, sl, inputs, flush) if not args.no_extra else None
     serving = serving_leg(args.serve_jobs, rank, ws) if (not args.no_extra and args.serve_jobs > 0) else None
     # the configured arrival rate offers several times what the device can serve (the FP64 jobs
     # alone take most of it), so its latencies are queueing times; the same trace at a rate the
@@ -526,6 +633,9 @@ def main():
         "multistep_200": multistep,
         "batched": batched,
         "deform3d_256": deform3d,
+        "integrators": integrators,
+        "burgers2d": burgers,
+        "quintic_z2": quintic,
         "serving": serving,
         "serving_sustained_rate": serving_light,
         "serving_fifo_uncapped": serving_fifo,

@@ -54,8 +54,14 @@ typedef enum {
 } sl_status;
 
 enum { SL_F64 = 0, SL_F32 = 1 };                       /* dtype of field planes and of D          */
-enum { SL_RK4 = 0 };                                   /* trajectory integrator                    */
-enum {                                                 /* analytic velocity u(x, t)               */
+enum {                                                 /* trajectory integrator (eq. vel)         */
+    SL_RK4 = 0,             /* classical 4-stage Runge-Kutta                                        */
+    SL_WRK3 = 1             /* Williamson's low-storage 3-stage, third-order Runge-Kutta (Sec. 2,
+                               the paper's integrator): A = (0, -5/9, -153/128),
+                               B = (1/3, 15/16, 8/15), stage times t, t + h/3, t + 3h/4            */
+};
+#define SL_MAX_SUBSTEPS 16                             /* trajectory sub-steps per remap (max)     */
+enum {                                                 /* velocity u(x, t) of eq. (vel)           */
     SL_VEL_UNIFORM = 0,     /* params (u, v[, w])                                                   */
     SL_VEL_SOLID_BODY = 1,  /* params (Omega, cx, cy): u = Omega (cy - y, x - cx)      (Sec. 3.1) */
     SL_VEL_SWIRL2D = 2,     /* params (T): u = sin^2(pi x) sin(2pi y) cos(pi t/T),
@@ -64,8 +70,15 @@ enum {                                                 /* analytic velocity u(x,
                                            v, w the cyclic permutations with amplitude -1        */
     SL_VEL_FOURIER2D = 4,   /* params (q, [kx ky a b] * q): u = d psi/dy, v = -d psi/dx with
                                            psi = sum a cos(2pi k.x) + b sin(2pi k.x), q <= 16    */
-    SL_VEL_FOURIER3D = 5    /* params (q, [k(3) a(3) b(3)] * q): u = curl of
+    SL_VEL_FOURIER3D = 5,   /* params (q, [k(3) a(3) b(3)] * q): u = curl of
                                            A = sum a cos(2pi k.x) + b sin(2pi k.x), q <= 8       */
+    SL_VEL_CARRIED = 6      /* params () or (f_x, f_y[, f_z]): the velocity is transported by the
+                               nodes as fields f_a (default the first dim fields; Sec. 3.2, Burgers:
+                               Du/Dt = 0, so each node moves on the straight line X + t u(X) and
+                               every integrator gives D = dt u / dx).  The trajectories need the
+                               fields: sl_step reads them at the start of each step, and
+                               sl_advect_nodes_carried replaces sl_advect_nodes.  Not fused into
+                               the tiled remap and not batched.                                 */
 };
 enum { SL_NEWTON_F64 = 0, SL_NEWTON_MIXED = 1 };       /* precision of the element-map inversion  */
 enum { SL_FAIL_KEEP = 0, SL_FAIL_ERROR = 1 };          /* what a failed target reports             */
@@ -80,9 +93,10 @@ typedef struct {
     double lo[3], hi[3];            /* periodic box                                                  */
     int nfields;                    /* 1..8 fields advected together                                 */
     int dtype;                      /* SL_F64 or SL_F32                                              */
-    int max_order;                  /* m_max of the Z-spline: 0 (linear) or 1 (cubic)                */
+    int max_order;                  /* m_max of the Z-spline: 0 (linear), 1 (cubic) or 2 (quintic;
+                                       plain kernels only)                                          */
     double limiter_threshold;       /* 0.25 in the paper (Sec. 2.3); < 0 disables the limiter        */
-    int integrator;                 /* SL_RK4                                                        */
+    int integrator;                 /* SL_RK4 or SL_WRK3                                             */
     int velocity_kind;              /* SL_VEL_*                                                      */
     const double *velocity_params;  /* host array, copied by sl_create_grid                          */
     int n_velocity_params;
@@ -96,6 +110,11 @@ typedef struct {
                                        compiled for 4 CTAs per SM, 5: 32x32 pipelined (persistent,
                                        one CTA per SM staging the next tiles while it computes;
                                        1 above 4 fields; batches run 5 as 1)                      */
+    int trajectory_substeps;        /* integrator steps per remap (Sec. 2: the Lagrangian grid may
+                                       move for several time steps before the fields are
+                                       interpolated back): each step of length dt integrates the
+                                       trajectories with this many sub-steps of dt / substeps, then
+                                       remaps once.  <= 0 selects 1; at most SL_MAX_SUBSTEPS.   */
 } sl_grid_desc;
 
 /* Counters accumulated on the device since creation or the last sl_reset_diagnostics. */
@@ -130,9 +149,17 @@ size_t sl_grid_workspace_bytes(const sl_grid_desc *desc);
 sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspace, size_t ws_bytes, sl_grid **out);
 sl_status sl_destroy_grid(sl_grid *grid);
 
-/* eq. (vel): move every Lagrangian node from its reference position over [t, t+dt] with one RK4
- * step of the grid's velocity; writes the grid's current displacement D (cell units). */
+/* eq. (vel): move every Lagrangian node from its reference position over [t, t+dt] with the grid's
+ * integrator (trajectory_substeps steps of RK4 or of the low-storage RK3) in the grid's analytic
+ * velocity; writes the grid's current displacement D (cell units).  SL_ERR_ARG for a carried
+ * velocity (it needs the fields: sl_advect_nodes_carried). */
 sl_status sl_advect_nodes(sl_grid *grid, double t, double dt, void *stream);
+
+/* Sec. 3.2: trajectories of a grid whose velocity is carried (SL_VEL_CARRIED): every node moves
+ * over dt with the velocity it holds in the field planes `fields` (nfields device pointers, the
+ * grid's dtype; only the velocity components are read): D_i = dt u_i / dx in cell units, written
+ * to the grid's current displacement.  SL_ERR_ARG for any other velocity kind. */
+sl_status sl_advect_nodes_carried(sl_grid *grid, const void *const *fields, double dt, void *stream);
 
 /* Sec. 2 reset / Sec. 2.2-2.3 / eq. (multiZ): with the current D, compute the jump flags of `in`,
  * locate every reference node, invert the element map, choose the order and interpolate.

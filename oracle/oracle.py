@@ -30,7 +30,8 @@ _lib = None
 
 # target status codes (oracle-local)
 OK, LOCATE, NEWTON, FOLD = 0, 1, 2, 3
-VELOCITY_KINDS = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5}
+VELOCITY_KINDS = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5,
+                  "carried": 6}
 START_PAPER, START_BACKWARD = 0, 1
 
 
@@ -54,6 +55,7 @@ class _Grid(C.Structure):
         ("vel_kind", C.c_int), ("n_vel_params", C.c_int), ("vel_params", C.POINTER(C.c_double)),
         ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("walk_max", C.c_int),
         ("slack", C.c_double), ("start_mode", C.c_int), ("fail_keep", C.c_int), ("nthreads", C.c_int),
+        ("integrator", C.c_int), ("substeps", C.c_int),
     ]
 
 
@@ -75,6 +77,7 @@ def _load():
         lib.or_flags.argtypes = [gp, dp, u8p]
         lib.or_velocity.argtypes = [gp, dp, C.c_double, dp]
         lib.or_advect.argtypes = [gp, C.c_double, C.c_double, dp]
+        lib.or_advect_carried.argtypes = [gp, dp, C.c_double, dp]
         lib.or_newton.argtypes = [C.c_int, dp, C.c_int, C.c_double, dp, C.POINTER(C.c_int)]
         lib.or_newton.restype = C.c_int
         lib.or_locate.argtypes = [gp, dp, i64p, i64p, dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -119,12 +122,15 @@ class OracleGrid:
     slack: float = 1e-12
     start: int = START_PAPER
     nthreads: int = 0
+    integrator: str = "rk4"       # "rk4" (classical) or "wrk3" (Williamson's low-storage RK3)
+    substeps: int = 1             # integrator steps of dt / substeps per remap
 
     def __post_init__(self):
         self.n = tuple(int(v) for v in self.n) + (1,) * (3 - len(self.n))
         self.lo = tuple(float(v) for v in self.lo) + (0.0,) * (3 - len(self.lo))
         self.hi = tuple(float(v) for v in self.hi) + (1.0,) * (3 - len(self.hi))
         self._params = np.ascontiguousarray(np.asarray(self.velocity_params, dtype=np.float64).ravel())
+        self._nparams = int(self._params.size)
         if self._params.size == 0:
             self._params = np.zeros(1)
 
@@ -145,10 +151,12 @@ class OracleGrid:
         g.hi[:] = list(self.hi)
         g.max_order, g.threshold = self.max_order, self.threshold
         g.vel_kind = VELOCITY_KINDS[self.velocity]
-        g.n_vel_params = int(self._params.size)
+        g.n_vel_params = self._nparams
         g.vel_params = _ptr(self._params, C.c_double)
         g.newton_max_iter, g.newton_tol, g.walk_max = self.newton_max_iter, self.newton_tol, self.walk_max
         g.slack, g.start_mode, g.fail_keep, g.nthreads = self.slack, self.start, 1, self.nthreads
+        g.integrator = {"rk4": 0, "wrk3": 1}[self.integrator]
+        g.substeps = int(self.substeps)
         return g
 
 
@@ -207,6 +215,17 @@ def advect(grid: OracleGrid, t: float, dt: float) -> np.ndarray:
     D = np.empty(grid.shape + (grid.dim,), dtype=np.float64)
     g = grid._c()
     _load().or_advect(C.byref(g), float(t), float(dt), _ptr(D, C.c_double))
+    return D
+
+
+def advect_carried(grid: OracleGrid, h, dt: float) -> np.ndarray:
+    """Displacement over dt of every node moving with the velocity it carries (velocity kind
+    "carried": the fields named by velocity_params, default the first dim fields), in cell units;
+    shape (*shape, dim)."""
+    h = _fields(grid, h)
+    D = np.empty(grid.shape + (grid.dim,), dtype=np.float64)
+    g = grid._c()
+    _load().or_advect_carried(C.byref(g), _ptr(h, C.c_double), float(dt), _ptr(D, C.c_double))
     return D
 
 

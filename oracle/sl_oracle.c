@@ -8,7 +8,9 @@
  * It shares no code, header, table or constant with the CUDA path, and the CUDA path never calls it.
  *
  * Every function restates one passage of the paper in plain loops, in the paper's order:
- *   Sec. 2, eqs. (momento)/(vel)        transport along trajectories (here: classical RK4, S = 0)
+ *   Sec. 2, eqs. (momento)/(vel)        transport along trajectories (classical RK4 or Williamson's
+ *                                       low-storage RK3, S = 0; the velocity either given or carried
+ *                                       by the nodes as transported fields, Sec. 3.2)
  *   Sec. 2.1, eq. (multiZ) + Appendix   cardinal Z-spline basis and its tensor-product sum
  *   Sec. 2.2, eq. (mapping1)            multilinear (Z0) element map, Newton inversion, element search
  *   Sec. 2.3                            jump criterion (limiter flags) and adaptive order reduction
@@ -43,9 +45,10 @@
 enum { OR_OK = 0, OR_LOCATE = 1, OR_NEWTON = 2, OR_FOLD = 3 };
 /* velocity kinds */
 enum { OR_VEL_UNIFORM = 0, OR_VEL_SOLID_BODY = 1, OR_VEL_SWIRL2D = 2, OR_VEL_DEFORM3D = 3,
-       OR_VEL_FOURIER2D = 4, OR_VEL_FOURIER3D = 5 };
+       OR_VEL_FOURIER2D = 4, OR_VEL_FOURIER3D = 5, OR_VEL_CARRIED = 6 };
 /* element-search start */
 enum { OR_START_PAPER = 0, OR_START_BACKWARD = 1 };
+enum { OR_RK4 = 0, OR_WRK3 = 1 };
 
 /* Grid and method parameters.  The Python wrapper mirrors this layout with ctypes. */
 typedef struct {
@@ -65,6 +68,8 @@ typedef struct {
     int start_mode;           /* OR_START_PAPER (default) */
     int fail_keep;            /* 1: a failed target keeps its old value (also done when 0; flag only) */
     int nthreads;             /* <= 0: library default */
+    int integrator;           /* OR_RK4 (classical) or OR_WRK3 (Williamson's low-storage RK3) */
+    int substeps;             /* integrator steps of dt / substeps per remap (<= 1: one)      */
 } or_grid;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -279,8 +284,72 @@ void or_velocity(const or_grid *g, const double x[3], double t, double u[3])
 /* ------------------------------------------------------------------------------------------ */
 /* eq. (vel): trajectory of every Lagrangian node over one step, classical RK4 from the         */
 /* reference position X_i at time t.  Output: displacement in cell units, D[i*dim + a].          */
+/* With substeps > 1 or the low-storage RK3, the position is carried through substeps steps of   */
+/* h = dt / substeps (Sec. 2: the Lagrangian grid may move for several time steps before the     */
+/* fields are interpolated back); the low-storage RK3 is Williamson's (J. Comp. Phys. 35, 1980)  */
+/* three-stage scheme q <- A_k q + h u(x, t_s + c_k h), x <- x + B_k q with                        */
+/* A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15) and stage times c = (0, 1/3, 3/4).            */
+/* A carried velocity (ucar != NULL: the node's own velocity, a transported field with no source, */
+/* so constant along the trajectory) replaces the analytic one at every stage.                    */
 /* ------------------------------------------------------------------------------------------ */
-void or_advect(const or_grid *g, double t, double dt, double *D)
+static void stage_velocity(const or_grid *g, const double *ucar, const double x[3], double t, double u[3])
+{
+    if (ucar) {
+        for (int a = 0; a < 3; ++a) u[a] = ucar[a];
+    } else {
+        or_velocity(g, x, t, u);
+    }
+}
+
+static void trajectory_substeps(const or_grid *g, const double *ucar, const double X[3], double t, double dt,
+                                double x[3])
+{
+    const int d = g->dim, S = g->substeps > 1 ? g->substeps : 1;
+    const double h = dt / (double)S;
+    for (int a = 0; a < 3; ++a) x[a] = X[a];
+    for (int st = 0; st < S; ++st) {
+        const double ts = t + (double)st * h;
+        if (g->integrator == OR_WRK3) {
+            double q[3] = {0, 0, 0}, u[3];
+            stage_velocity(g, ucar, x, ts, u);
+            for (int a = 0; a < d; ++a) {
+                q[a] = h * u[a];
+                x[a] += (1.0 / 3.0) * q[a];
+            }
+            stage_velocity(g, ucar, x, ts + h / 3.0, u);
+            for (int a = 0; a < d; ++a) {
+                q[a] = (-5.0 / 9.0) * q[a] + h * u[a];
+                x[a] += (15.0 / 16.0) * q[a];
+            }
+            stage_velocity(g, ucar, x, ts + 0.75 * h, u);
+            for (int a = 0; a < d; ++a) {
+                q[a] = (-153.0 / 128.0) * q[a] + h * u[a];
+                x[a] += (8.0 / 15.0) * q[a];
+            }
+        } else {
+            double k1[3], k2[3], k3[3], k4[3], y[3] = {0, 0, 0};
+            stage_velocity(g, ucar, x, ts, k1);
+            for (int a = 0; a < d; ++a) y[a] = x[a] + 0.5 * h * k1[a];
+            stage_velocity(g, ucar, y, ts + 0.5 * h, k2);
+            for (int a = 0; a < d; ++a) y[a] = x[a] + 0.5 * h * k2[a];
+            stage_velocity(g, ucar, y, ts + 0.5 * h, k3);
+            for (int a = 0; a < d; ++a) y[a] = x[a] + h * k3[a];
+            stage_velocity(g, ucar, y, ts + h, k4);
+            for (int a = 0; a < d; ++a) x[a] += h / 6.0 * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
+        }
+    }
+}
+
+/* Field plane holding velocity component a of a carried velocity: parameter a when given, else a. */
+static int carried_field(const or_grid *g, int a)
+{
+    return g->n_vel_params > a ? (int)g->vel_params[a] : a;
+}
+
+/* Sec. 3.2 (Burgers): the velocity is one of the transported fields, Du/Dt = 0, so every node moves
+ * with the value it carries: D_i = trajectory of X_i at the constant velocity u_i (the fields h are
+ * those at the start of the step, nfields planes of N values). */
+void or_advect_carried(const or_grid *g, const double *h, double dt, double *D)
 {
     int64_t N = total_nodes(g);
     int d = g->dim;
@@ -291,9 +360,37 @@ void or_advect(const or_grid *g, double t, double dt, double *D)
     for (int64_t i = 0; i < N; ++i) {
         int64_t k[3];
         node_coords(g, i, k);
+        double X[3] = {0, 0, 0}, u[3] = {0, 0, 0}, x[3];
+        for (int a = 0; a < d; ++a) {
+            X[a] = g->lo[a] + (double)k[a] * dx[a];
+            u[a] = h[(int64_t)carried_field(g, a) * N + i];
+        }
+        trajectory_substeps(g, u, X, 0.0, dt, x);
+        for (int a = 0; a < d; ++a) D[i * d + a] = (x[a] - X[a]) / dx[a];
+    }
+}
+
+void or_advect(const or_grid *g, double t, double dt, double *D)
+{
+    int64_t N = total_nodes(g);
+    int d = g->dim;
+    double dx[3];
+    for (int a = 0; a < d; ++a) dx[a] = (g->hi[a] - g->lo[a]) / (double)g->n[a];
+    const int general = g->integrator == OR_WRK3 || g->substeps > 1;
+    set_threads(g);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t k[3];
+        node_coords(g, i, k);
         double X[3] = {0, 0, 0}, y[3] = {0, 0, 0};
         double k1[3], k2[3], k3[3], k4[3];
         for (int a = 0; a < d; ++a) X[a] = g->lo[a] + (double)k[a] * dx[a];
+        if (general) {
+            double x[3];
+            trajectory_substeps(g, NULL, X, t, dt, x);
+            for (int a = 0; a < d; ++a) D[i * d + a] = (x[a] - X[a]) / dx[a];
+            continue;
+        }
         or_velocity(g, X, t, k1);
         for (int a = 0; a < d; ++a) y[a] = X[a] + 0.5 * dt * k1[a];
         or_velocity(g, y, t + 0.5 * dt, k2);
@@ -565,7 +662,10 @@ int64_t or_step(const or_grid *g, double *h, double t0, double dt, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         double t = t0 + (double)s * dt;
         or_flags(g, h, flags);
-        or_advect(g, t, dt, D);
+        if (g->vel_kind == OR_VEL_CARRIED)
+            or_advect_carried(g, h, dt, D);
+        else
+            or_advect(g, t, dt, D);
         nfail += or_remap(g, D, flags, h, tmp, NULL, NULL, NULL, NULL, NULL, NULL);
         memcpy(h, tmp, sizeof(double) * (size_t)N * (size_t)g->nfields);
     }

@@ -46,7 +46,8 @@ static const char *check_desc(const sl_grid_desc *d)
     if (d->nfields < 1 || d->nfields > SL_MAX_FIELDS) return "nfields must be in [1, 8]";
     if (d->dtype != SL_F64 && d->dtype != SL_F32) return "dtype must be SL_F64 or SL_F32";
     if (d->max_order < 0 || d->max_order > 2) return "max_order must be 0, 1 or 2";
-    if (d->integrator != SL_RK4) return "integrator must be SL_RK4";
+    if (d->integrator != SL_RK4 && d->integrator != SL_WRK3) return "integrator must be SL_RK4 or SL_WRK3";
+    if (d->trajectory_substeps > SL_MAX_SUBSTEPS) return "trajectory_substeps must be <= SL_MAX_SUBSTEPS";
     if (d->newton_mode != SL_NEWTON_F64 && d->newton_mode != SL_NEWTON_MIXED) return "bad newton_mode";
     if (d->newton_mode == SL_NEWTON_MIXED && d->dtype != SL_F32) return "SL_NEWTON_MIXED needs dtype SL_F32";
     if (d->fail_policy != SL_FAIL_KEEP && d->fail_policy != SL_FAIL_ERROR) return "bad fail_policy";
@@ -81,6 +82,17 @@ static const char *check_desc(const sl_grid_desc *d)
         if (d->dim != 3 || np < 1) return "fourier3d is 3-D";
         const int q = (int)p[0];
         if ((double)q != p[0] || q < 1 || q > 8 || np < 1 + 9 * q) return "fourier3d needs 1..8 modes of 9 values";
+        break;
+    }
+    case SL_VEL_CARRIED: {
+        if (np != 0 && np != d->dim) return "carried velocity takes no parameter or one field index per axis";
+        if (np == 0 && d->nfields < d->dim) return "carried velocity needs dim fields";
+        for (int a = 0; a < np; ++a) {
+            if (!isfinite(p[a]) || p[a] != (double)(int)p[a] || p[a] < 0 || p[a] >= d->nfields)
+                return "carried velocity field indices must be integers in [0, nfields)";
+            for (int b = 0; b < a; ++b)
+                if (p[b] == p[a]) return "carried velocity field indices must be distinct";
+        }
         break;
     }
     default:
@@ -170,6 +182,9 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     g->dcur = 0;
     const int vk = desc->velocity_kind;
     g->steady = vk == SL_VEL_UNIFORM || vk == SL_VEL_SOLID_BODY || vk == SL_VEL_FOURIER2D || vk == SL_VEL_FOURIER3D;
+    g->carried = vk == SL_VEL_CARRIED;
+    for (int a = 0; a < 3; ++a)
+        g->vel_field[a] = (g->carried && desc->n_velocity_params > a) ? (int)desc->velocity_params[a] : a;
     g->d_cached = 0;
     g->next_valid = 0;
     cudaError_t e = cudaGetDevice(&g->device);
@@ -220,6 +235,7 @@ extern "C" sl_status sl_advect_nodes(sl_grid *g, double t, double dt, void *stre
 {
     if (!g) return fail_arg("grid is NULL");
     if (!isfinite(t) || !isfinite(dt)) return fail_arg("t and dt must be finite");
+    if (g->carried) return fail_arg("a carried velocity needs the fields: call sl_advect_nodes_carried");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = g->dtype == SL_F64 ? Launch<double>::advect(g, g->D[g->dcur], t, dt, s)
                                        : Launch<float>::advect(g, g->D[g->dcur], t, dt, s);
@@ -228,6 +244,21 @@ extern "C" sl_status sl_advect_nodes(sl_grid *g, double t, double dt, void *stre
     g->d_cached_dt = dt;
     g->next_valid = 0;
     return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_advect_nodes");
+}
+
+extern "C" sl_status sl_advect_nodes_carried(sl_grid *g, const void *const *fields, double dt, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (!g->carried) return fail_arg("the grid's velocity is not carried by its fields");
+    if (sl_status st = check_planes(g, fields, "field planes")) return st;
+    if (!isfinite(dt)) return fail_arg("dt must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = g->dtype == SL_F64 ? Launch<double>::advect_carried(g, fields, g->D[g->dcur], dt, s)
+                                       : Launch<float>::advect_carried(g, fields, g->D[g->dcur], dt, s);
+    e = counted(g, e, 1);
+    g->d_cached = 0;
+    g->next_valid = 0;
+    return e == cudaSuccess ? SL_OK : fail_cuda(e, "sl_advect_nodes_carried");
 }
 
 template <typename T>
@@ -286,7 +317,10 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
         nxt[q] = scratch[q];
     }
     cudaError_t e = cudaSuccess;
-    const bool fused = use_tiled<T>(g);
+    // a carried velocity is read from the fields at the start of each step, so the next step's
+    // trajectories are not known inside this step's remap: carried steps are not fused
+    const bool carried = g->carried != 0;
+    const bool fused = use_tiled<T>(g) && !carried;
     // steady velocity: one integration serves every step (and later calls with the same dt)
     const bool reuse = g->steady != 0;
     if (reuse && !(g->d_cached && g->d_cached_dt == dt)) {
@@ -324,6 +358,12 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
                     g->next_valid = 1;
                 }
             }
+        } else if (carried) {
+            e = counted(g, Launch<T>::advect_carried(g, cur, g->D[g->dcur], dt, s), 1);
+            g->d_cached = 0;
+            g->next_valid = 0;
+            if (e == cudaSuccess) e = remap_impl<T>(g, g->D[g->dcur], cur, nxt, nullptr, s);
+            if (e != cudaSuccess) return e;
         } else {
             e = counted(g, Launch<T>::flags(g, cur, g->flags, s), 1);
             if (e == cudaSuccess && !reuse) {

@@ -33,15 +33,24 @@ struct BatchGrid {
     int tiles_x, tile_base;
 };
 
-// cos(pi t / period) at the RK4 stage times of a step starting at t (as the single-grid host code)
-__device__ __forceinline__ void stage_factors(const BatchGrid &g, double t, float ct[3])
+// cos(pi t / period) at the stage times of every trajectory sub-step of a step starting at t (the
+// single-grid host code fills the same table): sub-step s starts at t + s h, h = dt / substeps, and
+// its stages sit at c = (0, 1/2, 1) of h for RK4, (0, 1/3, 3/4) for Williamson's RK3
+__device__ __forceinline__ void stage_factors(const BatchGrid &g, double t, float *ct)
 {
+    const int ns = g.vel.substeps;
     if (g.period > 0.0) {
-        ct[0] = (float)cospi(t / g.period);
-        ct[1] = (float)cospi((t + 0.5 * g.dt) / g.period);
-        ct[2] = (float)cospi((t + g.dt) / g.period);
+        const double h = g.dt / ns;
+        const bool w3 = g.vel.integrator == SL_WRK3;
+        const double c1 = w3 ? 1.0 / 3.0 : 0.5, c2 = w3 ? 0.75 : 1.0;
+        for (int st = 0; st < ns; ++st) {
+            const double ts = t + (double)st * h;
+            ct[3 * st + 0] = (float)cospi(ts / g.period);
+            ct[3 * st + 1] = (float)cospi((ts + c1 * h) / g.period);
+            ct[3 * st + 2] = (float)cospi((ts + c2 * h) / g.period);
+        }
     } else {
-        ct[0] = ct[1] = ct[2] = 0.f;
+        for (int q = 0; q < 3 * ns; ++q) ct[q] = 0.f;
     }
 }
 
@@ -124,7 +133,7 @@ __global__ void __launch_bounds__(Cfg::NT)
             const int jx = tx * Cfg::TX + q % Cfg::TX, jy = ty * Cfg::TY + q / Cfg::TX;
             if (jx >= sg.base.n0 || jy >= sg.base.n1) continue;
             float X[3] = {sv.lo[0] + (float)jx * sv.dx[0], sv.lo[1] + (float)jy * sv.dx[1], 0.f}, d[3];
-            rk4_cells<float, 2>(sv, X, d);
+            trajectory_cells<float, 2>(sv, X, d);
             D[(long long)jy * sg.base.n0 + jx] = make_float2(d[0], d[1]);
         }
     }
@@ -213,9 +222,12 @@ struct sl_batch {
     std::vector<cudaGraphExec_t> graphs;
 };
 
+// the batch computes each step's RK4 stage factors on the device from the grid's time: one
+// classical RK4 step per remap only
 static bool batch_eligible(const sl_grid *g)
 {
-    return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.max_order <= 1 && g->desc.walk_start == SL_START_BACKWARD;
+    return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.max_order <= 1 && g->desc.walk_start == SL_START_BACKWARD &&
+           !g->carried;
 }
 
 extern "C" size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config)

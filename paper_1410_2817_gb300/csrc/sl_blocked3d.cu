@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
         if (FUSED && a.D_next != nullptr) {
             float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], vn.lo[2] + (float)jz * vn.dx[2]};
             float d[3];
-            rk4_cells<float, 3>(vn, X, d);
+            trajectory_cells<float, 3>(vn, X, d);
             a.D_next[jj] = make_float4(d[0], d[1], d[2], 0.f);
         }
     }

@@ -2,7 +2,8 @@
 // kernels of libsl.so.  Everything is templated on the arithmetic type T (double or float) and on
 // the dimension DIM (2 or 3).
 //
-//   velocity / rk4_cells     eq. (vel): analytic velocities and one classical RK4 step
+//   velocity / rk4_cells /   eq. (vel): analytic velocities, one classical RK4 step, and
+//   trajectory_cells         sub-stepped RK4 or Williamson's low-storage RK3
 //   newton_solve             Sec. 2.2, eq. (mapping1): inversion of the Z~0 (multilinear) map
 //   zspline / zs_weights     Appendix: cardinal Z-spline basis Z~0 (hat), Z~1, Z~2
 //   jump test                Sec. 2.3: |h+ - 2h + h-| > thr * max(|h+ - h|, |h - h-|)
@@ -30,8 +31,12 @@ template <typename T>
 struct VelArgs {
     int kind;
     int nmodes;
+    int integrator;   // SL_RK4 or SL_WRK3
+    int substeps;     // integrator steps of dt / substeps per step (1 .. SL_MAX_SUBSTEPS)
     T p[SL_MAX_VEL_PARAMS];
-    T ct[3];          // cos(pi t/T) at the RK4 stage times t, t + dt/2, t + dt (time-dependent flows)
+    // cos(pi t/T) at the stage times of sub-step s in ct[3 s + 0..2] (time-dependent flows):
+    // RK4 t_s, t_s + h/2, t_s + h; WRK3 t_s, t_s + h/3, t_s + 3h/4 (h = dt / substeps)
+    T ct[3 * SL_MAX_SUBSTEPS];
     T lo[3], dx[3], inv_dx[3];
     T dt;
 };
@@ -200,6 +205,74 @@ __device__ __forceinline__ void velocity(const VelArgs<T> &v, const T x[3], int 
 
 // One classical RK4 step of eq. (vel) from the reference position X over [t, t + dt]; returns the
 // displacement in cell units.
+template <typename T, int DIM>
+__device__ __forceinline__ void rk4_cells(const VelArgs<T> &v, const T X[3], T out[3]);
+
+// eq. (vel) over [t, t + dt] from the reference position X with `substeps` steps of h = dt/substeps
+// of classical RK4 or of Williamson's low-storage RK3 (two registers per component: q, e):
+//   q <- A_k q + h u(X + e, t_s + c_k h),  e <- e + B_k q,  A = (0, -5/9, -153/128),
+//   B = (1/3, 15/16, 8/15), c = (0, 1/3, 3/4);
+// returns the displacement e in cell units.  The displacement, not the position, is accumulated:
+// in FP32 a position near 1 would round every update to ~6e-8 of the box.  One RK4 step is
+// rk4_cells itself.
+template <typename T, int DIM>
+__device__ __forceinline__ void trajectory_cells(const VelArgs<T> &v, const T X[3], T out[3])
+{
+    if (v.integrator == SL_RK4 && v.substeps == 1) {
+        rk4_cells<T, DIM>(v, X, out);
+        return;
+    }
+    const T h = v.dt / T(v.substeps);
+    T e[3] = {T(0), T(0), T(0)}, y[3] = {X[0], X[1], X[2]}, k[3];
+    for (int st = 0; st < v.substeps; ++st) {
+        if (v.integrator == SL_WRK3) {
+            T q[3];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) y[a] = X[a] + e[a];
+            velocity<T, DIM>(v, y, 3 * st + 0, k);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                q[a] = h * k[a];
+                e[a] += T(1.0 / 3.0) * q[a];
+                y[a] = X[a] + e[a];
+            }
+            velocity<T, DIM>(v, y, 3 * st + 1, k);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                q[a] = T(-5.0 / 9.0) * q[a] + h * k[a];
+                e[a] += T(15.0 / 16.0) * q[a];
+                y[a] = X[a] + e[a];
+            }
+            velocity<T, DIM>(v, y, 3 * st + 2, k);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                q[a] = T(-153.0 / 128.0) * q[a] + h * k[a];
+                e[a] += T(8.0 / 15.0) * q[a];
+            }
+        } else {
+            T k1[3], k2[3], k3[3];
+            const T hh = T(0.5) * h;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) y[a] = X[a] + e[a];
+            velocity<T, DIM>(v, y, 3 * st + 0, k1);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) y[a] = X[a] + (e[a] + hh * k1[a]);
+            velocity<T, DIM>(v, y, 3 * st + 1, k2);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) y[a] = X[a] + (e[a] + hh * k2[a]);
+            velocity<T, DIM>(v, y, 3 * st + 1, k3);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) y[a] = X[a] + (e[a] + h * k3[a]);
+            velocity<T, DIM>(v, y, 3 * st + 2, k);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) e[a] += h / T(6) * (k1[a] + T(2) * k2[a] + T(2) * k3[a] + k[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) out[a] = e[a] * v.inv_dx[a];
+    if (DIM == 2) out[2] = T(0);
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ void rk4_cells(const VelArgs<T> &v, const T X[3], T out[3])
 {
@@ -372,34 +445,59 @@ __device__ __forceinline__ int newton_solve(const T P[8][3], int max_iter, T tol
 }
 
 // ------------------------------------------------------------------------------------------------
-// Appendix: cardinal Z-spline basis functions (piecewise form, any argument)
+// Appendix: cardinal Z-spline basis functions (piecewise form, any argument).  The quintic's three
+// pieces are evaluated in the local variable of their own interval, where the Horner coefficients
+// stay below 6: P1(a) on [0, 1], P2(1 + s) and P3(3 - u) with s, u in [0, 1].  (Expanded in |x|,
+// the outer piece sums terms of ~350 to values of ~1e-2, which in FP32 leaves errors of ~2e-5.)
 // ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T z2_inner(T a)  // |x| = a in [0, 1]
+{
+    return T(1) + a * a * (T(-1.25) + a * (T(-35.0 / 12.0) + a * (T(5.25) + a * T(-25.0 / 12.0))));
+}
+template <typename T>
+__device__ __forceinline__ T z2_middle(T s)  // |x| = 1 + s, s in [0, 1]
+{
+    return s * (T(-2.0 / 3.0) + s * (T(2.0 / 3.0) + s * (T(1.625) + s * (T(-8.0 / 3.0) + s * T(25.0 / 24.0)))));
+}
+template <typename T>
+__device__ __forceinline__ T z2_outer(T u)  // |x| = 3 - u, u in [0, 1]
+{
+    return u * u * u * (T(7.0 / 24.0) + u * (T(-0.5) + u * T(5.0 / 24.0)));
+}
+
 template <typename T>
 __device__ __forceinline__ T zspline(int m, T x)
 {
-    const T ax = abs_t(x), x2 = ax * ax, x3 = x2 * ax;
+    const T ax = abs_t(x);
     if (m == 0) return ax < T(1) ? T(1) - ax : T(0);
     if (m == 1) {
+        const T x2 = ax * ax, x3 = x2 * ax;
         if (ax <= T(1)) return T(1) - T(2.5) * x2 + T(1.5) * x3;
         if (ax <= T(2)) return T(0.5) * (T(2) - ax) * (T(2) - ax) * (T(1) - ax);
         return T(0);
     }
-    const T x4 = x3 * ax, x5 = x4 * ax;
-    if (ax <= T(1))
-        return T(1) - T(15.0 / 12.0) * x2 - T(35.0 / 12.0) * x3 + T(63.0 / 12.0) * x4 - T(25.0 / 12.0) * x5;
-    if (ax <= T(2))
-        return T(-4) + T(75.0 / 4.0) * ax - T(245.0 / 8.0) * x2 + T(545.0 / 24.0) * x3 - T(63.0 / 8.0) * x4
-               + T(25.0 / 24.0) * x5;
-    if (ax <= T(3))
-        return T(18) - T(153.0 / 4.0) * ax + T(255.0 / 8.0) * x2 - T(313.0 / 24.0) * x3 + T(21.0 / 8.0) * x4
-               - T(5.0 / 24.0) * x5;
+    if (ax <= T(1)) return z2_inner(ax);
+    if (ax <= T(2)) return z2_middle(ax - T(1));
+    if (ax <= T(3)) return z2_outer(T(3) - ax);
     return T(0);
 }
 
 // Weights of the 2m+2 taps c-m .. c+m+1 at local coordinate xi (argument of tap k: m - k + xi).
+// For the quintic each tap's piece is known from k, and its local variable is xi or 1 - xi.
 template <typename T>
 __device__ __forceinline__ void zs_weights(int m, T xi, T w[6])
 {
+    if (m == 2) {
+        const T y = T(1) - xi;
+        w[0] = z2_outer(y);
+        w[1] = z2_middle(xi);
+        w[2] = z2_inner(xi);
+        w[3] = z2_inner(y);
+        w[4] = z2_middle(y);
+        w[5] = z2_outer(xi);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] = (k < 2 * m + 2) ? zspline<T>(m, T(m - k) + xi) : T(0);
 }

@@ -35,6 +35,9 @@ struct sl_grid {
     // so a call that starts there skips its own integration.
     int next_valid;
     VelArgs<float> next_vel;
+    // A carried velocity (SL_VEL_CARRIED) lives in field planes vel_field[a] of the fields.
+    int carried;
+    int vel_field[3];
 };
 
 #define SL_MOMENT_BLOCKS 512
@@ -43,6 +46,7 @@ struct sl_grid {
 template <typename T>
 struct Launch {
     static cudaError_t advect(const sl_grid *g, void *D, double t, double dt, cudaStream_t s);
+    static cudaError_t advect_carried(const sl_grid *g, const void *const *fields, void *D, double dt, cudaStream_t s);
     static cudaError_t flags(const sl_grid *g, const void *const *in, uint8_t *flags, cudaStream_t s);
     static cudaError_t remap_generic(const sl_grid *g, const void *D, const uint8_t *flags, const void *const *in,
                                      void *const *out, const sl_remap_debug *dbg, cudaStream_t s);

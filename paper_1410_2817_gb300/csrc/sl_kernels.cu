@@ -53,12 +53,26 @@ VelArgs<T> make_vel_args(const sl_grid *g, double t, double dt)
     memset(&v, 0, sizeof(v));
     v.kind = g->desc.velocity_kind;
     v.nmodes = (v.kind == SL_VEL_FOURIER2D || v.kind == SL_VEL_FOURIER3D) ? (int)g->vel_params[0] : 0;
+    v.integrator = g->desc.integrator;
+    v.substeps = g->desc.trajectory_substeps > 0 ? g->desc.trajectory_substeps : 1;
     for (int q = 0; q < SL_MAX_VEL_PARAMS; ++q) v.p[q] = (T)g->vel_params[q];
     if (v.kind == SL_VEL_SWIRL2D || v.kind == SL_VEL_DEFORM3D) {
         const double period = g->vel_params[0];
-        v.ct[0] = (T)cospi_host(t / period);
-        v.ct[1] = (T)cospi_host((t + 0.5 * dt) / period);
-        v.ct[2] = (T)cospi_host((t + dt) / period);
+        if (v.integrator == SL_RK4 && v.substeps == 1) {
+            v.ct[0] = (T)cospi_host(t / period);
+            v.ct[1] = (T)cospi_host((t + 0.5 * dt) / period);
+            v.ct[2] = (T)cospi_host((t + dt) / period);
+        } else {
+            // stage times of sub-step s: t_s + c h with t_s = t + s h, h = dt / substeps
+            const double h = dt / v.substeps;
+            const double c1 = v.integrator == SL_WRK3 ? 1.0 / 3.0 : 0.5, c2 = v.integrator == SL_WRK3 ? 0.75 : 1.0;
+            for (int st = 0; st < v.substeps; ++st) {
+                const double ts = t + (double)st * h;
+                v.ct[3 * st + 0] = (T)cospi_host(ts / period);
+                v.ct[3 * st + 1] = (T)cospi_host((ts + c1 * h) / period);
+                v.ct[3 * st + 2] = (T)cospi_host((ts + c2 * h) / period);
+            }
+        }
     }
     for (int q = 0; q < 3; ++q) {
         v.lo[q] = (T)g->desc.lo[q];
@@ -159,10 +173,35 @@ __global__ void __launch_bounds__(256) advect_kernel(GridArgs<T> g, VelArgs<T> v
         T X[3] = {T(0), T(0), T(0)}, d[3];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) X[a] = v.lo[a] + T(k[a]) * v.dx[a];
-        rk4_cells<T, DIM>(v, X, d);
+        trajectory_cells<T, DIM>(v, X, d);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) D[i * ds + a] = d[a];
         if (DIM == 3) D[i * ds + 3] = T(0);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Sec. 3.2: the velocity carried by the nodes (Burgers, Du/Dt = 0) is constant along each
+// trajectory, so every integrator moves node i by dt u_i: D_i = (dt / dx_a) u_a,i in cell units.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256)
+    advect_carried_kernel(long long N, const T *__restrict__ u0, const T *__restrict__ u1, const T *__restrict__ u2,
+                          T s0, T s1, T s2, T *__restrict__ D)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (DIM == 2) {
+            using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+            T2 d;
+            d.x = s0 * __ldg(u0 + i);
+            d.y = s1 * __ldg(u1 + i);
+            reinterpret_cast<T2 *>(D)[i] = d;
+        } else {
+            D[i * 4 + 0] = s0 * __ldg(u0 + i);
+            D[i * 4 + 1] = s1 * __ldg(u1 + i);
+            D[i * 4 + 2] = s2 * __ldg(u2 + i);
+            D[i * 4 + 3] = T(0);
+        }
     }
 }
 
@@ -524,6 +563,23 @@ cudaError_t Launch<T>::advect(const sl_grid *g, void *D, double t, double dt, cu
         advect_kernel<T, 2><<<blocks, 256, 0, s>>>(ga, va, (T *)D, g->ds);
     else
         advect_kernel<T, 3><<<blocks, 256, 0, s>>>(ga, va, (T *)D, g->ds);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::advect_carried(const sl_grid *g, const void *const *fields, void *D, double dt, cudaStream_t s)
+{
+    const T *u[3] = {nullptr, nullptr, nullptr};
+    T sc[3] = {T(0), T(0), T(0)};
+    for (int a = 0; a < g->dim; ++a) {
+        u[a] = (const T *)fields[g->vel_field[a]];
+        sc[a] = (T)(dt / g->dx[a]);
+    }
+    const int blocks = grid_stride_blocks(g, g->N, 256);
+    if (g->dim == 2)
+        advect_carried_kernel<T, 2><<<blocks, 256, 0, s>>>(g->N, u[0], u[1], u[1], sc[0], sc[1], sc[2], (T *)D);
+    else
+        advect_carried_kernel<T, 3><<<blocks, 256, 0, s>>>(g->N, u[0], u[1], u[2], sc[0], sc[1], sc[2], (T *)D);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,8 @@ flat parameter vector:
 * ``deform3d``    (T,):                     3-D deformation flow, period T
 * ``fourier2d``   (nmodes, [kx, ky, a, b] * nmodes): streamfunction of Fourier modes
 * ``fourier3d``   (nmodes, [k(3), a(3), b(3)] * nmodes): curl of a Fourier vector potential
+* ``carried``     ([field index per axis]):  the velocity is itself transported by the nodes
+                                            (Burgers, Sec. 3.2); default the first dim fields
 """
 from __future__ import annotations
 
@@ -103,6 +105,29 @@ def workload_swirl(n: int = 1024, steps: int = 200, cfl: float = 5.0) -> Workloa
     """2-D swirl u = sin^2(pi x) sin(2 pi y) cos(pi t/T), v = -sin^2(pi y) sin(2 pi x) cos(pi t/T),
     T = 5; dt = cfl * dx / max|u| with max|u| = 1."""
     return Workload(f"swirl2d_{n}", 2, (n, n), 3, "swirl2d", [5.0], cfl / n, steps, fields=swirl_fields(n))
+
+
+# ---------------------------------------------------------------------------------------------
+# 2-D inviscid Burgers (Sec. 3.2): the two velocity components are the transported fields
+# ---------------------------------------------------------------------------------------------
+def burgers_fields(n) -> np.ndarray:
+    """Radial pulse u = exp(-150 (r - 0.2)^2) (x - 1/2, y - 1/2) / r about the box centre (zero
+    for r <= 0.001), the initial condition of Sec. 3.2; |u| <= 1.  n: side, or (nx, ny)."""
+    x, y = node_coords((n, n) if np.isscalar(n) else tuple(n))
+    rx, ry = x - 0.5, y - 0.5
+    r = np.hypot(rx, ry)
+    amp = np.where(r > 0.001, np.exp(-150.0 * (r - 0.2) ** 2) / np.maximum(r, 0.001), 0.0)
+    return np.stack([amp * rx, amp * ry])
+
+
+def workload_burgers(n: int = 1024, steps: int | None = None, cfl: float = 0.5, t_end: float = 0.4) -> Workload:
+    """2-D Burgers on the unit square: dt = cfl * dx / max|u| (max|u| = 1; cfl < 1 keeps the
+    converging elements at the shock unfolded for one step); by default enough steps to reach
+    t_end = 0.4, the last time the paper shows."""
+    dt = cfl / n
+    if steps is None:
+        steps = int(math.ceil(t_end / dt))
+    return Workload(f"burgers2d_{n}", 2, (n, n), 2, "carried", [], dt, steps, fields=burgers_fields(n))
 
 
 # ---------------------------------------------------------------------------------------------

@@ -21,8 +21,10 @@ LIB_PATH = os.path.join(_PKG, "libsl.so")
 SL_OK, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_NOMEM, SL_ERR_BUDGET = 0, 1, 2, 3, 4
 SL_ERR_LOCATE, SL_ERR_NEWTON, SL_ERR_FOLD, SL_ERR_UNSUPPORTED = 5, 6, 7, 8
 SL_F64, SL_F32 = 0, 1
-SL_RK4 = 0
-VELOCITY = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5}
+SL_RK4, SL_WRK3 = 0, 1
+SL_MAX_SUBSTEPS = 16
+INTEGRATOR = {"rk4": SL_RK4, "wrk3": SL_WRK3}
+VELOCITY = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5, "carried": 6}
 SL_NEWTON_F64, SL_NEWTON_MIXED = 0, 1
 SL_FAIL_KEEP, SL_FAIL_ERROR = 0, 1
 SL_START_BACKWARD, SL_START_PAPER = 0, 1
@@ -44,7 +46,7 @@ class sl_grid_desc(C.Structure):
         ("integrator", C.c_int), ("velocity_kind", C.c_int), ("velocity_params", C.POINTER(C.c_double)),
         ("n_velocity_params", C.c_int), ("newton_mode", C.c_int), ("newton_max_iter", C.c_int),
         ("walk_max", C.c_int), ("fail_policy", C.c_int), ("walk_start", C.c_int), ("kernel", C.c_int),
-        ("tile_config", C.c_int),
+        ("tile_config", C.c_int), ("trajectory_substeps", C.c_int),
     ]
 
 
@@ -85,6 +87,7 @@ def lib():
             "sl_create_grid": (C.c_int, [C.POINTER(sl_grid_desc), vp, C.c_size_t, C.POINTER(vp)]),
             "sl_destroy_grid": (C.c_int, [vp]),
             "sl_advect_nodes": (C.c_int, [vp, C.c_double, C.c_double, vp]),
+            "sl_advect_nodes_carried": (C.c_int, [vp, pp, C.c_double, vp]),
             "sl_remap_fields": (C.c_int, [vp, pp, pp, vp]),
             "sl_remap_fields_debug": (C.c_int, [vp, pp, pp, C.POINTER(sl_remap_debug), vp]),
             "sl_step": (C.c_int, [vp, pp, pp, C.c_double, C.c_double, C.c_int, vp]),
@@ -152,7 +155,8 @@ def _planes(ts):
 def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), max_order=1,
               limiter_threshold=0.25, velocity="uniform", velocity_params=(0.0, 0.0, 0.0),
               newton_mode=None, newton_max_iter=0, walk_max=0, fail_policy=SL_FAIL_KEEP,
-              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO, tile_config=0):
+              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO, tile_config=0, integrator=SL_RK4,
+              trajectory_substeps=0):
     d = sl_grid_desc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -161,7 +165,8 @@ def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1
     d.hi[:] = [float(v) for v in list(hi) + [1.0] * (3 - len(hi))]
     d.nfields, d.dtype, d.max_order = nfields, dtype, max_order
     d.limiter_threshold = float(limiter_threshold)
-    d.integrator = SL_RK4
+    d.integrator = INTEGRATOR[integrator] if isinstance(integrator, str) else int(integrator)
+    d.trajectory_substeps = int(trajectory_substeps)
     d.velocity_kind = VELOCITY[velocity] if isinstance(velocity, str) else int(velocity)
     params = (C.c_double * max(1, len(velocity_params)))(*[float(v) for v in velocity_params])
     d.velocity_params = C.cast(params, C.POINTER(C.c_double))
@@ -191,6 +196,11 @@ def sl_destroy_grid(h):
 
 def sl_advect_nodes(h, t: float, dt: float, stream=None):
     _check(lib().sl_advect_nodes(h, float(t), float(dt), _stream(stream)), "sl_advect_nodes")
+
+
+def sl_advect_nodes_carried(h, fields: Sequence[torch.Tensor], dt: float, stream=None):
+    pf, _a = _planes(fields)
+    _check(lib().sl_advect_nodes_carried(h, pf, float(dt), _stream(stream)), "sl_advect_nodes_carried")
 
 
 def sl_remap_fields(h, fin: Sequence[torch.Tensor], fout: Sequence[torch.Tensor], stream=None):
@@ -297,6 +307,10 @@ class Grid:
 
     def advect(self, t, dt, stream=None):
         sl_advect_nodes(self.handle, t, dt, stream)
+
+    def advect_carried(self, fields, dt, stream=None):
+        """Trajectories of a carried velocity (velocity="carried"): D = dt u / dx from the fields."""
+        sl_advect_nodes_carried(self.handle, self._fit(fields), dt, stream)
 
     def _fit(self, planes):
         """The nfields planes of this grid (a stacked tensor or a sequence); others raise."""

@@ -52,9 +52,24 @@ def test_workspace_bytes_and_validation(libsl):
         sl.make_desc(2, (64, 64), 1, sl.SL_F64, newton_mode=sl.SL_NEWTON_MIXED),
         sl.make_desc(2, (64, 64), 1, velocity="fourier2d", velocity_params=[3.0, 1, 1, 0.5, 0.5]),
         sl.make_desc(2, (64, 64), 1, velocity="swirl2d", velocity_params=[0.0]),
+        sl.make_desc(2, (64, 64), 1, integrator=2),
+        sl.make_desc(2, (64, 64), 1, velocity="carried", velocity_params=[]),        # fewer fields than axes
+        sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[0]),       # one index in 2-D
+        sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[0, 3]),    # index out of range
+        sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[1, 1]),    # repeated index
+        sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[0, 1.5]),  # not an integer
+        sl.make_desc(2, (64, 64), 1, trajectory_substeps=sl.SL_MAX_SUBSTEPS + 1),
     ]
     for b in bad:
         assert sl.sl_grid_workspace_bytes(b) == 0
+    for ok in (sl.make_desc(2, (64, 64), 1, integrator="wrk3"),
+               sl.make_desc(2, (64, 64), 1, trajectory_substeps=sl.SL_MAX_SUBSTEPS),
+               sl.make_desc(3, (8, 8, 8), 1, velocity="deform3d", velocity_params=[3.0], integrator="wrk3",
+                            trajectory_substeps=3),
+               sl.make_desc(2, (64, 64), 2, velocity="carried", velocity_params=[]),
+               sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[2, 0]),
+               sl.make_desc(3, (8, 8, 8), 3, velocity="carried", velocity_params=[])):
+        assert sl.sl_grid_workspace_bytes(ok) > 0
 
 
 def test_create_rejects_bad_workspace_without_gpu(libsl):

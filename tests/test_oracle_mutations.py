@@ -46,6 +46,19 @@ MUTATIONS = {
                              "test_oracle_limiter.py"),
     "failed_target_value": ("h_out[(int64_t)f * N + jj] = h_in[(int64_t)f * N + jj];", "h_out[(int64_t)f * N + jj] = 0.0;",
                             "test_oracle_remap.py"),
+    "wrk3_coefficient": ("q[a] = (-5.0 / 9.0) * q[a] + h * u[a];", "q[a] = (-4.0 / 9.0) * q[a] + h * u[a];",
+                         "test_oracle_advect.py"),
+    "wrk3_stage_time": ("stage_velocity(g, ucar, x, ts + h / 3.0, u);", "stage_velocity(g, ucar, x, ts + 0.5 * h, u);",
+                        "test_oracle_advect.py"),
+    "wrk3_update_weight": ("x[a] += (8.0 / 15.0) * q[a];", "x[a] += (7.0 / 15.0) * q[a];", "test_oracle_advect.py"),
+    "substep_time": ("const double ts = t + (double)st * h;", "const double ts = t;", "test_oracle_advect.py"),
+    "carried_component": ("u[a] = h[(int64_t)carried_field(g, a) * N + i];", "u[a] = h[i];",
+                          "test_oracle_burgers.py"),
+    "carried_index": ("return g->n_vel_params > a ? (int)g->vel_params[a] : a;", "return a;",
+                      "test_oracle_burgers.py"),
+    "carried_sign": ("for (int a = 0; a < d; ++a) D[i * d + a] = (x[a] - X[a]) / dx[a];\n    }\n}",
+                     "for (int a = 0; a < d; ++a) D[i * d + a] = (X[a] - x[a]) / dx[a];\n    }\n}",
+                     "test_oracle_burgers.py"),
     "moment_centre": ("cen[a] = 0.5 * (g->lo[a] + g->hi[a]);", "cen[a] = 0.5 * (g->hi[a] - g->lo[a]);",
                       "test_oracle_step.py"),
 }
