@@ -328,35 +328,37 @@ def integrators_leg(torch, sl, inputs, flush, steps=10):
 
 def quintic_leg(torch, sl, inputs, flush, steps=10):
     """The headline workload with the quintic Z2 (six points per axis, orders 2 -> 1 -> 0 near
-    jumps): FP32 on the plain kernels (flags, RK4, remap: three launches per step), L2 flushed
-    before each step."""
+    jumps), FP32, L2 flushed before each step: the tiled quintic kernel with the next step's
+    trajectories fused in (`tiled`), and the plain kernels (flags, RK4, remap) for comparison."""
     wl = inputs.workload_swirl(N_SIDE)
     wl.max_order = 2
-    g = sl.grid_for(wl, sl.SL_F32)
-    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
-    s = torch.empty_like(f)
-    t = 0.0
-    for _ in range(3):
-        g.step(f, s, t, wl.dt, 1)
-        t += wl.dt
-    l0 = g.diagnostics()["kernel_launches"]
-    ev = []
-    for q in range(steps):
-        flush.fill_(q & 0xff)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.step(f, s, t, wl.dt, 1)
-        b.record()
-        ev.append((a, b))
-        t += wl.dt
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-    d = g.diagnostics()
-    out = {"workload": f"swirl2d {N_SIDE}^2 x 3 fields, Z2, FP32 plain kernels", "ms_per_step": ms,
-           "value": wl.nnodes / (ms * 1e-3), "unit": UNIT, "launches_per_step": (d["kernel_launches"] - l0) / steps,
-           "order_hist": d["order_hist"],
-           "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"]}
-    g.close()
+    out = {"workload": f"swirl2d {N_SIDE}^2 x 3 fields, Z2, FP32"}
+    for name, kern in (("tiled", sl.SL_KERNEL_AUTO), ("plain", sl.SL_KERNEL_GENERIC)):
+        g = sl.grid_for(wl, sl.SL_F32, kernel=kern)
+        f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+        s = torch.empty_like(f)
+        t = 0.0
+        for _ in range(3):
+            g.step(f, s, t, wl.dt, 1)
+            t += wl.dt
+        l0 = g.diagnostics()["kernel_launches"]
+        ev = []
+        for q in range(steps):
+            flush.fill_(q & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.step(f, s, t, wl.dt, 1)
+            b.record()
+            ev.append((a, b))
+            t += wl.dt
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        d = g.diagnostics()
+        out[name] = {"ms_per_step": ms, "value": wl.nnodes / (ms * 1e-3), "unit": UNIT,
+                     "launches_per_step": (d["kernel_launches"] - l0) / steps, "order_hist": d["order_hist"],
+                     "tiles_fallback": d["tiles_fallback"],
+                     "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"]}
+        g.close()
     return out
 
 

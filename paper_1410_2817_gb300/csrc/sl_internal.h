@@ -85,6 +85,10 @@ size_t tiled2d_smem_bytes_cfgc(int nfields);
 cudaError_t launch_tiled2d_cfgd(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                                 const void *const *in, void *const *out, cudaStream_t s);
 size_t tiled2d_smem_bytes_cfgd(int nfields);
+// 2-D FP32 tiled kernels of the quintic Z-spline (max_order 2; sl_tiled_z2.cu)
+cudaError_t launch_tiled2d_z2(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
+                              const void *const *in, void *const *out, cudaStream_t s);
+size_t tiled2d_smem_bytes_z2(int nfields);
 
 // shared argument builders (sl_kernels.cu)
 template <typename T>

@@ -495,6 +495,48 @@ __device__ __forceinline__ void clear_flags(const TileArgs &a, const Win &w, uns
     }
 }
 
+// Sec. 2.3: jump flags of the window's interior nodes (rows and columns 1 .. w-2) into the bit
+// plane M (one bit per node and field, `plane` words per field, `nwx` words per row), set with a
+// shared-memory atomic: flagged nodes are few.  M must be clear; the caller synchronises after.
+template <class Cfg, int NF>
+__device__ __forceinline__ void flag_window(const TileArgs &a, const Win &w, const float4 *sH, unsigned *sM, int nwx,
+                                            int plane)
+{
+    constexpr int NT = Cfg::NT, WMAX = Cfg::WMAX;
+    constexpr int NG = groups(NF);
+    const int iw = w.wx - 2, ni = iw * (w.wy - 2);
+    const float inv_iw = 1.f / (float)max(iw, 1);
+    for (int q = threadIdx.x; q < ni; q += NT) {
+        const int r = row_of(q, inv_iw), y = r + 1, x = q - r * iw + 1;
+        const int idx = y * w.wx + x;
+        unsigned bits = 0;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const float4 *h = sH + g * WMAX;
+            const float4 c = h[idx];
+            if (in_group(NF, g) == 4)
+                bits |= (jump4<4>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<4>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                        << (4 * g);
+            else if (in_group(NF, g) == 3)
+                bits |= (jump4<3>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<3>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                        << (4 * g);
+            else if (in_group(NF, g) == 2)
+                bits |= (jump4<2>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<2>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                        << (4 * g);
+            else
+                bits |= (jump4<1>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<1>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
+                        << (4 * g);
+        }
+        if (bits) {
+            unsigned *m = sM + y * nwx + (x >> 5);
+            const unsigned bit = 1u << (x & 31);
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                if ((bits >> f) & 1u) atomicOr(m + f * plane, bit);
+        }
+    }
+}
+
 // Phases 3 and 4 of one tile whose window (sD, sH) and start points (sS) are in shared memory and
 // whose flag plane M is clear: every thread of the CTA calls this; it synchronises the CTA.
 template <class Cfg, int NF>
@@ -512,37 +554,7 @@ __device__ __forceinline__ void tile_compute(const TileArgs &a, int x0, int y0, 
     // shared-memory atomic: flagged nodes are few); then B = M ORed over 4 rows and bits x-1 .. x+2.
     const int nwx = (w.wx + 31) >> 5, plane = w.wy * nwx;
     if (limit) {
-        const int iw = w.wx - 2, ni = iw * (w.wy - 2);
-        const float inv_iw = 1.f / (float)max(iw, 1);
-        for (int q = threadIdx.x; q < ni; q += NT) {
-            const int r = row_of(q, inv_iw), y = r + 1, x = q - r * iw + 1;
-            const int idx = y * w.wx + x;
-            unsigned bits = 0;
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                const float4 *h = sH + g * WMAX;
-                const float4 c = h[idx];
-                if (in_group(NF, g) == 4)
-                    bits |= (jump4<4>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<4>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
-                            << (4 * g);
-                else if (in_group(NF, g) == 3)
-                    bits |= (jump4<3>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<3>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
-                            << (4 * g);
-                else if (in_group(NF, g) == 2)
-                    bits |= (jump4<2>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<2>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
-                            << (4 * g);
-                else
-                    bits |= (jump4<1>(h[idx - 1], c, h[idx + 1], a.thr) | jump4<1>(h[idx - w.wx], c, h[idx + w.wx], a.thr))
-                            << (4 * g);
-            }
-            if (bits) {
-                unsigned *m = sM + y * nwx + (x >> 5);
-                const unsigned bit = 1u << (x & 31);
-#pragma unroll
-                for (int f = 0; f < NF; ++f)
-                    if ((bits >> f) & 1u) atomicOr(m + f * plane, bit);
-            }
-        }
+        flag_window<Cfg, NF>(a, w, sH, sM, nwx, plane);
         __syncthreads();
         // rows 2 .. wy-4 (the elements whose stencil lies in the interior rows 1 .. wy-2)
         const int brows = w.wy - 5;

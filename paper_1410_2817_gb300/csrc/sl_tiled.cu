@@ -1,6 +1,6 @@
 // sl_tiled.cu -- dispatch of the FP32 production kernels: 2-D grids go to the shared-memory tiled
-// kernels (sl_tile2d.cuh, one translation unit per tile configuration), 3-D grids to the blocked
-// kernels (sl_blocked3d.cu).
+// kernels (sl_tile2d.cuh, one translation unit per tile configuration; the quintic Z-spline to
+// sl_tiled_z2.cu), 3-D grids to the blocked kernels (sl_blocked3d.cu, cubic and linear only).
 #include <string.h>
 
 #include "sl_internal.h"
@@ -11,7 +11,8 @@ int tiled_kernels_per_call(const sl_grid *g) { return g->dim == 2 ? 1 : 3; }
 template <typename T>
 bool Launch<T>::tiled_supported(const sl_grid *g)
 {
-    if (sizeof(T) != 4 || g->desc.max_order > 1 || g->desc.walk_start != SL_START_BACKWARD) return false;
+    if (sizeof(T) != 4 || g->desc.walk_start != SL_START_BACKWARD) return false;
+    if (g->desc.max_order > 1) return g->dim == 2 && tiled2d_smem_bytes_z2(g->nfields) <= 200 * 1024;
     if (g->dim == 3) return g->N < (1LL << 31);  // the blocked kernel forms 32-bit node offsets
     const int c = g->desc.tile_config;
     const size_t smem = c == 2   ? tiled2d_smem_bytes_cfgb(g->nfields)
@@ -24,6 +25,7 @@ bool Launch<T>::tiled_supported(const sl_grid *g)
 static cudaError_t launch_tiled2d(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                                   const void *const *in, void *const *out, cudaStream_t s)
 {
+    if (g->desc.max_order > 1) return launch_tiled2d_z2(g, D, D_next, t_next, dt, fused, in, out, s);
     switch (g->desc.tile_config) {
     case 5:
         if (g->nfields <= 4) return launch_tiled2d_cfgp(g, D, D_next, t_next, dt, fused, in, out, s);

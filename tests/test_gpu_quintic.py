@@ -131,3 +131,97 @@ def test_full_size_sampled(sl, orc, dtype):
                 assert abs(got[q, jy, jx] - v) <= 1e-12 * max(1.0, abs(v))
     if dtype == "f32":
         assert worst <= 5e-5, worst
+
+
+def _shear_displacement(n, a):
+    x, y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    D = np.zeros((n, n, 2))
+    D[..., 0] = a * n / (2 * np.pi) * np.sin(2 * np.pi * y / n)
+    D[..., 1] = a * n / (2 * np.pi) * np.sin(2 * np.pi * x / n)
+    return D
+
+
+@pytest.mark.parametrize("case", ["swirl", "smooth_ragged", "shear_fallback", "limiter_off", "five_fields",
+                                  "one_field"])
+def test_tiled_matches_generic_f32(sl, orc, case):
+    """The quintic tiled FP32 kernel (staged window, 6x6 and 4x4 flag boxes, 6x6 taps) computes what
+    the plain FP32 kernel computes: the same elements and orders away from faces, values up to the
+    weight polynomials' and the summation order's rounding; tiles whose window does not fit run on
+    global memory (shear case)."""
+    rng = np.random.default_rng(31)
+    thr = 0.25
+    if case == "swirl":
+        n = (256, 256)
+        og = orc.OracleGrid(dim=2, n=n, nfields=3, velocity="swirl2d", velocity_params=[5.0])
+        D, h = orc.advect(og, 0.9, 5 / 256), inputs.swirl_fields(256)
+    elif case == "smooth_ragged":
+        n = (75, 53)
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=3, shift=(2.3, -1.7))
+        h = np.stack([rng.standard_normal((53, 75)).cumsum(axis=1) * 0.1, (rng.uniform(size=(53, 75)) > 0.5) * 1.0])
+    elif case == "shear_fallback":
+        n = (256, 256)
+        D = _shear_displacement(256, 0.9)
+        h = inputs.swirl_fields(256)[:2]
+    elif case == "limiter_off":
+        n, thr = (64, 96), -1.0
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=4, shift=(0.4, 4.2))
+        h = rng.standard_normal((4, 96, 64))
+    elif case == "five_fields":
+        n = (96, 70)
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=12, shift=(2.2, 1.3))
+        h = np.stack([rng.standard_normal((70, 96)).cumsum(axis=1) * 0.1 for _ in range(5)])
+        h[0] += (np.arange(96)[None, :] > 48) * 1.0
+    else:
+        n = (40, 40)
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=7, shift=(-1.2, 3.4))
+        h = rng.standard_normal((1, 40, 40)).cumsum(axis=2) * 0.1
+    nf = h.shape[0]
+    outs, diags = {}, {}
+    for kname, kern in (("generic", sl.SL_KERNEL_GENERIC), ("tiled", sl.SL_KERNEL_TILED)):
+        g = sl.Grid(2, n, nf, sl.SL_F32, max_order=2, limiter_threshold=thr, walk_start=sl.SL_START_BACKWARD,
+                    kernel=kern)
+        hin = torch.tensor(h, dtype=torch.float32, device=DEV)
+        hout = torch.empty_like(hin)
+        g.set_displacement(torch.tensor(D, dtype=torch.float32, device=DEV))
+        g.remap(hin, hout)
+        torch.cuda.synchronize()
+        outs[kname] = hout.double().cpu().numpy()
+        diags[kname] = g.diagnostics()
+    scale = max(1.0, float(np.abs(h).max()))
+    diff = np.abs(outs["tiled"] - outs["generic"])
+    dg, dt = diags["generic"], diags["tiled"]
+    ntar = n[0] * n[1]
+    # after the displacement copy: tiled one launch; plain flags + remap
+    assert dt["kernel_launches"] == 1 + 1 and dg["kernel_launches"] == 1 + 2
+    assert float((diff > 4e-6 * scale).mean()) <= 1e-4, float(diff.max())
+    assert dt["targets"] == dg["targets"] == ntar
+    assert max(abs(a - b) for a, b in zip(dt["order_hist"], dg["order_hist"])) <= max(2, 1e-4 * ntar)
+    if case == "swirl":  # smooth Gaussian and sine, a step: all three orders occur
+        assert min(dt["order_hist"]) > 0
+    if case == "shear_fallback":
+        assert dt["tiles_fallback"] > 0
+    else:
+        tiles = -(-n[0] // 32) * -(-n[1] // 32)
+        assert dt["tiles_fallback"] <= 0.1 * tiles
+
+
+def test_fused_tiled_step_matches_plain_f32(sl):
+    """sl_step with Z2 on the tiled path: one launch per step (the next step's trajectories inside
+    the remap launch), the plain FP32 path's values step by step."""
+    wl = inputs.workload_swirl(192, steps=4)
+    wl.max_order = 2
+    gt = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_AUTO)
+    gg = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_GENERIC)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
+    t, worst = 0.25, 0.0
+    for _ in range(3):
+        ft, fg = f.clone(), f.clone()
+        gt.step(ft, torch.empty_like(ft), t, wl.dt, 2)
+        gg.step(fg, torch.empty_like(fg), t, wl.dt, 2)
+        torch.cuda.synchronize()
+        d = (ft - fg).abs()
+        assert float((d > 4e-6).float().mean()) <= 1e-4, float(d.max())
+        f, t = fg, t + 2 * wl.dt
+    l0 = gt.diagnostics()["kernel_launches"]
+    gt.step(f, torch.empty_like(f), 0.0, wl.dt, 6)
+    assert gt.diagnostics()["kernel_launches"] - l0 == 1 + 6
