@@ -31,7 +31,7 @@ _lib = None
 # target status codes (oracle-local)
 OK, LOCATE, NEWTON, FOLD = 0, 1, 2, 3
 VELOCITY_KINDS = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5,
-                  "carried": 6}
+                  "carried": 6, "nlsw": 7}
 START_PAPER, START_BACKWARD = 0, 1
 
 

@@ -15,6 +15,9 @@
  *   Sec. 2.2, eq. (mapping1)            multilinear (Z0) element map, Newton inversion, element search
  *   Sec. 2.3                            jump criterion (limiter flags) and adaptive order reduction
  *   Sec. 3.1, moments definition        discrete moments m_p (Table 1)
+ *   Sec. 3.3, eq. (nlsw)                shallow-water sources (pressure gradient, divergence,
+ *                                       Coriolis) by finite differences on the node lattice,
+ *                                       integrated with the low-storage RK3, then the remap
  *
  * Readings where the paper is silent or garbled (each is also listed with the design notes):
  *   - Z0 is not printed; it is the hat max(0, 1-|x|).
@@ -45,7 +48,7 @@
 enum { OR_OK = 0, OR_LOCATE = 1, OR_NEWTON = 2, OR_FOLD = 3 };
 /* velocity kinds */
 enum { OR_VEL_UNIFORM = 0, OR_VEL_SOLID_BODY = 1, OR_VEL_SWIRL2D = 2, OR_VEL_DEFORM3D = 3,
-       OR_VEL_FOURIER2D = 4, OR_VEL_FOURIER3D = 5, OR_VEL_CARRIED = 6 };
+       OR_VEL_FOURIER2D = 4, OR_VEL_FOURIER3D = 5, OR_VEL_CARRIED = 6, OR_VEL_NLSW = 7 };
 /* element-search start */
 enum { OR_START_PAPER = 0, OR_START_BACKWARD = 1 };
 enum { OR_RK4 = 0, OR_WRK3 = 1 };
@@ -644,10 +647,124 @@ int or_eval_in_element(const or_grid *g, const double *D, const uint8_t *flags, 
     return st;
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Sec. 3.3, eq. (nlsw), nu = 0: the non-dimensional shallow-water system on the moving nodes,    */
+/*   Dh/Dt = -(1 + h) div u,   Du/Dt = -grad h - f u_perp,   u_perp = (-u2, u1),  f = f0 x2,      */
+/* with h, u1, u2 the fields 0, 1, 2 (further fields are passive) and vel_params = (f0).          */
+/* Sec. 2: spatial derivatives by finite differences on the reference grid, time by Williamson's */
+/* low-storage RK3 over the step, then the reset (remap).  Readings: the step starts with the    */
+/* nodes on the reference grid and remaps once; at every stage the derivatives are taken on the */
+/* node lattice (the reference grid's stencil applied to the nodes' current values, i.e. in the */
+/* reference coordinates X) and turned into physical ones by the chain rule with the Jacobian   */
+/* J = dx/dX = I + de/dX of the node positions (de/dX by the same differences), so that          */
+/* grad h = J^-T dh/dX and div u = tr(du/dX J^-1); the node moves with its own current velocity; */
+/* f is taken at the node's current position.  The                                               */
+/* difference is that of the Z-spline basis of order m_max (Sec. 2.1: Z-splines are the          */
+/* collocation basis of finite differences): the derivative at a node of the interpolant,        */
+/* sum_k w_k Z'(-k) / dx, i.e. the second-order centred difference for m <= 1 (Z1'(1) = -1/2) and */
+/* the fourth-order one for m = 2 (Z2'(1) = -2/3, Z2'(2) = 1/12).                                */
+/* ------------------------------------------------------------------------------------------ */
+static double lattice_derivative(const or_grid *g, const double *w, const int64_t k[3], int a, double dxa)
+{
+    int64_t kp[3] = {k[0], k[1], k[2]}, km[3] = {k[0], k[1], k[2]};
+    kp[a] += 1;
+    km[a] -= 1;
+    const double d1 = w[node_index(g, kp)] - w[node_index(g, km)];
+    if (g->max_order < 2) return 0.5 * d1 / dxa;
+    kp[a] += 1;
+    km[a] -= 1;
+    const double d2 = w[node_index(g, kp)] - w[node_index(g, km)];
+    return ((2.0 / 3.0) * d1 - (1.0 / 12.0) * d2) / dxa;
+}
+
+/* One step of the shallow-water system: h (nfields planes) is replaced by the remapped fields.
+ * Scratch: W (nfields planes), q (3 planes), e and qx (2 planes each), D (2 per node),
+ * flags (N), tmp (nfields planes).  Returns the failed targets of the remap. */
+static int64_t or_nlsw_step(const or_grid *g, double *h, double dt, double *W, double *q, double *e, double *qx,
+                            double *D, uint8_t *flags, double *tmp)
+{
+    const int64_t N = total_nodes(g);
+    const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0}, B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+    const double f0 = g->vel_params[0];
+    double dx[2];
+    for (int a = 0; a < 2; ++a) dx[a] = (g->hi[a] - g->lo[a]) / (double)g->n[a];
+    memcpy(W, h, sizeof(double) * (size_t)N * (size_t)g->nfields);
+    memset(q, 0, sizeof(double) * (size_t)N * 3);
+    memset(e, 0, sizeof(double) * (size_t)N * 2);
+    memset(qx, 0, sizeof(double) * (size_t)N * 2);
+    const double *wh = W, *wu = W + N, *wv = W + 2 * N;
+    double *ex = e, *ey = e + N; /* node displacement (physical units), one plane per axis */
+    set_threads(g);
+    for (int s = 0; s < 3; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            int64_t k[3];
+            node_coords(g, i, k);
+            /* Jacobian of the node positions and its inverse */
+            const double J00 = 1.0 + lattice_derivative(g, ex, k, 0, dx[0]), J01 = lattice_derivative(g, ex, k, 1, dx[1]);
+            const double J10 = lattice_derivative(g, ey, k, 0, dx[0]), J11 = 1.0 + lattice_derivative(g, ey, k, 1, dx[1]);
+            const double det = J00 * J11 - J01 * J10;
+            const double I00 = J11 / det, I01 = -J01 / det, I10 = -J10 / det, I11 = J00 / det;
+            /* reference-coordinate derivatives */
+            const double hX = lattice_derivative(g, wh, k, 0, dx[0]), hY = lattice_derivative(g, wh, k, 1, dx[1]);
+            const double uX = lattice_derivative(g, wu, k, 0, dx[0]), uY = lattice_derivative(g, wu, k, 1, dx[1]);
+            const double vX = lattice_derivative(g, wv, k, 0, dx[0]), vY = lattice_derivative(g, wv, k, 1, dx[1]);
+            /* physical: grad h = J^-T (hX, hY); div u = du/dX_b (J^-1)_b0 + dv/dX_b (J^-1)_b1 */
+            const double hx = I00 * hX + I10 * hY, hy = I01 * hX + I11 * hY;
+            const double div = uX * I00 + uY * I10 + vX * I01 + vY * I11;
+            const double y = g->lo[1] + (double)k[1] * dx[1] + ey[i];
+            const double f = f0 * y;
+            const double S[3] = {-(1.0 + wh[i]) * div, -hx + f * wv[i], -hy - f * wu[i]};
+            for (int c = 0; c < 3; ++c) q[(int64_t)c * N + i] = A[s] * q[(int64_t)c * N + i] + dt * S[c];
+            qx[i] = A[s] * qx[i] + dt * wu[i];
+            qx[N + i] = A[s] * qx[N + i] + dt * wv[i];
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            for (int c = 0; c < 3; ++c) W[(int64_t)c * N + i] += B[s] * q[(int64_t)c * N + i];
+            ex[i] += B[s] * qx[i];
+            ey[i] += B[s] * qx[N + i];
+        }
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        D[2 * i + 0] = ex[i] / dx[0];
+        D[2 * i + 1] = ey[i] / dx[1];
+    }
+    or_flags(g, W, flags);
+    const int64_t nfail = or_remap(g, D, flags, W, tmp, NULL, NULL, NULL, NULL, NULL, NULL);
+    memcpy(h, tmp, sizeof(double) * (size_t)N * (size_t)g->nfields);
+    return nfail;
+}
+
+static int64_t or_nlsw_steps(const or_grid *g, double *h, double dt, int nsteps)
+{
+    const int64_t N = total_nodes(g);
+    const size_t F = (size_t)N * (size_t)g->nfields;
+    double *W = (double *)malloc(sizeof(double) * F), *tmp = (double *)malloc(sizeof(double) * F);
+    double *q = (double *)malloc(sizeof(double) * (size_t)N * 3);
+    double *e = (double *)malloc(sizeof(double) * (size_t)N * 2), *qx = (double *)malloc(sizeof(double) * (size_t)N * 2);
+    double *D = (double *)malloc(sizeof(double) * (size_t)N * 2);
+    uint8_t *flags = (uint8_t *)malloc((size_t)N);
+    int64_t nfail = 0;
+    if (W && tmp && q && e && qx && D && flags) {
+        for (int s = 0; s < nsteps; ++s) nfail += or_nlsw_step(g, h, dt, W, q, e, qx, D, flags, tmp);
+    } else {
+        nfail = -1;
+    }
+    free(W);
+    free(tmp);
+    free(q);
+    free(e);
+    free(qx);
+    free(D);
+    free(flags);
+    return nfail;
+}
+
 /* One full FSL step sequence: flags of the current fields, trajectories, remap.  h is updated
  * in place (nfields planes).  Returns the total number of failed targets. */
 int64_t or_step(const or_grid *g, double *h, double t0, double dt, int nsteps)
 {
+    if (g->vel_kind == OR_VEL_NLSW) return or_nlsw_steps(g, h, dt, nsteps);
     int64_t N = total_nodes(g);
     double *D = (double *)malloc(sizeof(double) * (size_t)N * (size_t)g->dim);
     double *tmp = (double *)malloc(sizeof(double) * (size_t)N * (size_t)g->nfields);

@@ -59,6 +59,14 @@ MUTATIONS = {
     "carried_sign": ("for (int a = 0; a < d; ++a) D[i * d + a] = (x[a] - X[a]) / dx[a];\n    }\n}",
                      "for (int a = 0; a < d; ++a) D[i * d + a] = (X[a] - x[a]) / dx[a];\n    }\n}",
                      "test_oracle_burgers.py"),
+    "nlsw_coriolis_sign": ("-hy - f * wu[i]}", "-hy + f * wu[i]}", "test_oracle_nlsw.py"),
+    "nlsw_depth_factor": ("-(1.0 + wh[i]) * div", "-div", "test_oracle_nlsw.py"),
+    "nlsw_difference": ("return ((2.0 / 3.0) * d1 - (1.0 / 12.0) * d2) / dxa;", "return (0.5 * d1 - (1.0 / 12.0) * d2) / dxa;",
+                        "test_oracle_nlsw.py"),
+    "nlsw_chain_rule": ("const double hx = I00 * hX + I10 * hY, hy = I01 * hX + I11 * hY;",
+                        "const double hx = hX, hy = hY;", "test_oracle_nlsw.py"),
+    "nlsw_node_velocity": ("qx[N + i] = A[s] * qx[N + i] + dt * wv[i];", "qx[N + i] = A[s] * qx[N + i] + dt * wu[i];",
+                           "test_oracle_nlsw.py"),
     "moment_centre": ("cen[a] = 0.5 * (g->lo[a] + g->hi[a]);", "cen[a] = 0.5 * (g->hi[a] - g->lo[a]);",
                       "test_oracle_step.py"),
 }
