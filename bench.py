@@ -362,6 +362,35 @@ def quintic_leg(torch, sl, inputs, flush, steps=10):
     return out
 
 
+def nlsw_leg(torch, sl, inputs, flush, steps=10):
+    """Shallow water (Sec. 3.3) on 1024^2: the paper's Kelvin-wave test (f0 = 250, amplitude 1e-4,
+    Z2, limiter off, dt = dx / 2), FP32.  Each step is three RK3 stages on the nodes (six launches:
+    sources by fourth-order differences through the node Jacobian, then the node update) and the
+    tiled quintic remap; L2 flushed before each step."""
+    wl = inputs.workload_kelvin(N_SIDE)
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    s = torch.empty_like(f)
+    g.step(f, s, 0.0, wl.dt, 3)
+    l0 = g.diagnostics()["kernel_launches"]
+    ev = []
+    for q in range(steps):
+        flush.fill_(q & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(f, s, 0.0, wl.dt, 1)
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    d = g.diagnostics()
+    out = {"workload": f"kelvin wave {N_SIDE}^2, fields (h, u1, u2), Z2, FP32", "ms_per_step": ms,
+           "value": wl.nnodes / (ms * 1e-3), "unit": UNIT, "launches_per_step": (d["kernel_launches"] - l0) / steps,
+           "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"]}
+    g.close()
+    return out
+
+
 def burgers_leg(torch, sl, inputs, flush, steps=10):
     """2-D inviscid Burgers (Sec. 3.2) on 1024^2, FP32: the two velocity components are the
     transported fields and every node moves with the velocity it carries (dt = dx / 2).  Each
@@ -595,6 +624,7 @@ def main():
     integrators = integrators_leg(torch, sl, inputs, flush) if not args.no_extra else None
     burgers = burgers_leg(torch, sl, inputs, flush) if not args.no_extra else None
     quintic = quintic_leg(torch, sl, inputs, flush) if not args.no_extra else None
+    nlsw = nlsw_leg(torch, sl, inputs, flush) if not args.no_extra else None
     serving = serving_leg(args.serve_jobs, rank, ws) if (not args.no_extra and args.serve_jobs > 0) else None
     # the configured arrival rate offers several times what the device can serve (the FP64 jobs
     # alone take most of it), so its latencies are queueing times; the same trace at a rate the
@@ -638,6 +668,7 @@ def main():
         "integrators": integrators,
         "burgers2d": burgers,
         "quintic_z2": quintic,
+        "nlsw_kelvin": nlsw,
         "serving": serving,
         "serving_sustained_rate": serving_light,
         "serving_fifo_uncapped": serving_fifo,

@@ -659,8 +659,8 @@ int or_eval_in_element(const or_grid *g, const double *D, const uint8_t *flags, 
 /* J = dx/dX = I + de/dX of the node positions (de/dX by the same differences), so that          */
 /* grad h = J^-T dh/dX and div u = tr(du/dX J^-1); the node moves with its own current velocity; */
 /* f is taken at the node's current position.  The                                               */
-/* difference is that of the Z-spline basis of order m_max (Sec. 2.1: Z-splines are the          */
-/* collocation basis of finite differences): the derivative at a node of the interpolant,        */
+/* difference is that of the Z-spline basis of order m_max (Sec. 2.1: differentiating a Z-spline  */
+/* interpolant at the nodes gives finite differences): the derivative at a node of the interpolant,*/
 /* sum_k w_k Z'(-k) / dx, i.e. the second-order centred difference for m <= 1 (Z1'(1) = -1/2) and */
 /* the fourth-order one for m = 2 (Z2'(1) = -2/3, Z2'(2) = 1/12).                                */
 /* ------------------------------------------------------------------------------------------ */

@@ -95,6 +95,12 @@ static const char *check_desc(const sl_grid_desc *d)
         }
         break;
     }
+    case SL_VEL_NLSW:
+        if (d->dim != 2 || d->nfields < 3) return "nlsw is 2-D with at least 3 fields (h, u1, u2)";
+        if (np != 1) return "nlsw takes one parameter (f0)";
+        if (d->integrator != SL_WRK3 || d->trajectory_substeps > 1)
+            return "nlsw integrates with SL_WRK3, one step per remap";
+        break;
     default:
         return "unknown velocity_kind";
     }
@@ -104,7 +110,7 @@ static const char *check_desc(const sl_grid_desc *d)
 }
 
 struct Layout {
-    size_t counters, partials, moment_out, flags, flags2, D0, D1, total;
+    size_t counters, partials, moment_out, flags, flags2, D0, D1, rk, total;
 };
 
 static Layout layout_of(const sl_grid_desc *d)
@@ -129,6 +135,9 @@ static Layout layout_of(const sl_grid_desc *d)
     off += align256((size_t)N * ds * ts);
     L.D1 = off;
     off += align256((size_t)N * ds * ts);
+    // shallow water: the RK3 registers of h, u1, u2 (three planes)
+    L.rk = off;
+    if (d->velocity_kind == SL_VEL_NLSW) off += align256((size_t)N * 3 * ts);
     L.total = off;
     return L;
 }
@@ -183,6 +192,8 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     const int vk = desc->velocity_kind;
     g->steady = vk == SL_VEL_UNIFORM || vk == SL_VEL_SOLID_BODY || vk == SL_VEL_FOURIER2D || vk == SL_VEL_FOURIER3D;
     g->carried = vk == SL_VEL_CARRIED;
+    g->nlsw = vk == SL_VEL_NLSW;
+    g->rk = vk == SL_VEL_NLSW ? (void *)(g->ws + L.rk) : nullptr;
     for (int a = 0; a < 3; ++a)
         g->vel_field[a] = (g->carried && desc->n_velocity_params > a) ? (int)desc->velocity_params[a] : a;
     g->d_cached = 0;
@@ -236,6 +247,7 @@ extern "C" sl_status sl_advect_nodes(sl_grid *g, double t, double dt, void *stre
     if (!g) return fail_arg("grid is NULL");
     if (!isfinite(t) || !isfinite(dt)) return fail_arg("t and dt must be finite");
     if (g->carried) return fail_arg("a carried velocity needs the fields: call sl_advect_nodes_carried");
+    if (g->nlsw) return fail_arg("shallow-water grids move their nodes inside sl_step");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = g->dtype == SL_F64 ? Launch<double>::advect(g, g->D[g->dcur], t, dt, s)
                                        : Launch<float>::advect(g, g->D[g->dcur], t, dt, s);
@@ -317,6 +329,19 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
         nxt[q] = scratch[q];
     }
     cudaError_t e = cudaSuccess;
+    if (g->nlsw) {
+        // three RK3 stages on the nodes (node values in the scratch planes), then the remap back
+        // into the caller's planes: the result lands in `fields` after every step
+        g->d_cached = 0;
+        g->next_valid = 0;
+        for (int k = 0; k < nsteps; ++k) {
+            e = counted(g, Launch<T>::nlsw_stages(g, (const void *const *)fields, scratch, g->D[g->dcur],
+                                                  g->D[g->dcur ^ 1], dt, s), 6);
+            if (e == cudaSuccess) e = remap_impl<T>(g, g->D[g->dcur], (const void *const *)scratch, fields, nullptr, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     // a carried velocity is read from the fields at the start of each step, so the next step's
     // trajectories are not known inside this step's remap: carried steps are not fused
     const bool carried = g->carried != 0;

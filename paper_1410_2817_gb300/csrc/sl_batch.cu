@@ -227,7 +227,7 @@ struct sl_batch {
 static bool batch_eligible(const sl_grid *g)
 {
     return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.max_order <= 1 && g->desc.walk_start == SL_START_BACKWARD &&
-           !g->carried;
+           !g->carried && !g->nlsw;
 }
 
 extern "C" size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config)

@@ -16,6 +16,7 @@ flat parameter vector:
 * ``fourier3d``   (nmodes, [k(3), a(3), b(3)] * nmodes): curl of a Fourier vector potential
 * ``carried``     ([field index per axis]):  the velocity is itself transported by the nodes
                                             (Burgers, Sec. 3.2); default the first dim fields
+* ``nlsw``        (f0,):                    shallow-water system of Sec. 3.3 on fields (h, u1, u2)
 """
 from __future__ import annotations
 
@@ -128,6 +129,30 @@ def workload_burgers(n: int = 1024, steps: int | None = None, cfl: float = 0.5, 
     if steps is None:
         steps = int(math.ceil(t_end / dt))
     return Workload(f"burgers2d_{n}", 2, (n, n), 2, "carried", [], dt, steps, fields=burgers_fields(n))
+
+
+# ---------------------------------------------------------------------------------------------
+# Shallow water (Sec. 3.3): the equatorial Kelvin wave, eq. (kelvin)
+# ---------------------------------------------------------------------------------------------
+def kelvin_fields(n: int, t: float = 0.0, amp: float = 1e-4, f0: float = 250.0) -> np.ndarray:
+    """h = u1 = exp(-f0 x2^2 / 2) K(x1 - t), u2 = 0 with K(s) = amp exp(-f0 s^2 / 2) (nearest
+    periodic image) on [0, 1] x [-0.5, 0.5], n x n nodes; planes (h, u1, u2)."""
+    x1 = np.arange(n) / n
+    x2 = -0.5 + np.arange(n) / n
+    X1, X2 = np.meshgrid(x1, x2)
+    s = (X1 - t + 0.5) % 1.0 - 0.5
+    h = np.exp(-f0 * X2 ** 2 / 2) * amp * np.exp(-f0 * s ** 2 / 2)
+    return np.stack([h, h, np.zeros_like(h)])
+
+
+def workload_kelvin(n: int = 1024, amp: float = 1e-4, f0: float = 250.0, cfl: float = 0.5,
+                    max_order: int = 2) -> Workload:
+    """The paper's Kelvin-wave test: f0 = 250, amplitude 1e-4, limiter off, to t = 1 (once round
+    the periodic box) with dt = cfl dx (unit wave speed)."""
+    steps = int(round(1.0 / (cfl / n)))
+    return Workload(f"kelvin_{n}", 2, (n, n), 3, "nlsw", [f0], 1.0 / steps, steps, lo=(0.0, -0.5, 0.0),
+                    hi=(1.0, 0.5, 1.0), max_order=max_order, threshold=-1.0,
+                    fields=kelvin_fields(n, 0.0, amp, f0))
 
 
 # ---------------------------------------------------------------------------------------------

@@ -24,7 +24,8 @@ SL_F64, SL_F32 = 0, 1
 SL_RK4, SL_WRK3 = 0, 1
 SL_MAX_SUBSTEPS = 16
 INTEGRATOR = {"rk4": SL_RK4, "wrk3": SL_WRK3}
-VELOCITY = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5, "carried": 6}
+VELOCITY = {"uniform": 0, "solid_body": 1, "swirl2d": 2, "deform3d": 3, "fourier2d": 4, "fourier3d": 5, "carried": 6,
+            "nlsw": 7}
 SL_NEWTON_F64, SL_NEWTON_MIXED = 0, 1
 SL_FAIL_KEEP, SL_FAIL_ERROR = 0, 1
 SL_START_BACKWARD, SL_START_PAPER = 0, 1
@@ -155,7 +156,7 @@ def _planes(ts):
 def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), max_order=1,
               limiter_threshold=0.25, velocity="uniform", velocity_params=(0.0, 0.0, 0.0),
               newton_mode=None, newton_max_iter=0, walk_max=0, fail_policy=SL_FAIL_KEEP,
-              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO, tile_config=0, integrator=SL_RK4,
+              walk_start=SL_START_BACKWARD, kernel=SL_KERNEL_AUTO, tile_config=0, integrator=None,
               trajectory_substeps=0):
     d = sl_grid_desc()
     d.dim = dim
@@ -165,6 +166,8 @@ def make_desc(dim, n, nfields, dtype=SL_F32, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1
     d.hi[:] = [float(v) for v in list(hi) + [1.0] * (3 - len(hi))]
     d.nfields, d.dtype, d.max_order = nfields, dtype, max_order
     d.limiter_threshold = float(limiter_threshold)
+    if integrator is None:  # the shallow-water system integrates with the paper's RK3
+        integrator = SL_WRK3 if velocity in ("nlsw", 7) else SL_RK4
     d.integrator = INTEGRATOR[integrator] if isinstance(integrator, str) else int(integrator)
     d.trajectory_substeps = int(trajectory_substeps)
     d.velocity_kind = VELOCITY[velocity] if isinstance(velocity, str) else int(velocity)

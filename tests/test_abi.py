@@ -58,6 +58,10 @@ def test_workspace_bytes_and_validation(libsl):
         sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[0, 3]),    # index out of range
         sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[1, 1]),    # repeated index
         sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[0, 1.5]),  # not an integer
+        sl.make_desc(2, (64, 64), 3, velocity="nlsw", velocity_params=[250.0], integrator="rk4"),
+        sl.make_desc(2, (64, 64), 2, velocity="nlsw", velocity_params=[250.0]),          # needs h, u1, u2
+        sl.make_desc(3, (8, 8, 8), 3, velocity="nlsw", velocity_params=[250.0]),         # 2-D only
+        sl.make_desc(2, (64, 64), 3, velocity="nlsw", velocity_params=[250.0], trajectory_substeps=2),
         sl.make_desc(2, (64, 64), 1, trajectory_substeps=sl.SL_MAX_SUBSTEPS + 1),
     ]
     for b in bad:
@@ -68,8 +72,13 @@ def test_workspace_bytes_and_validation(libsl):
                             trajectory_substeps=3),
                sl.make_desc(2, (64, 64), 2, velocity="carried", velocity_params=[]),
                sl.make_desc(2, (64, 64), 3, velocity="carried", velocity_params=[2, 0]),
-               sl.make_desc(3, (8, 8, 8), 3, velocity="carried", velocity_params=[])):
+               sl.make_desc(3, (8, 8, 8), 3, velocity="carried", velocity_params=[]),
+               sl.make_desc(2, (64, 64), 4, velocity="nlsw", velocity_params=[250.0])):
         assert sl.sl_grid_workspace_bytes(ok) > 0
+    # shallow-water grids also hold the RK3 registers of h, u1, u2
+    base = sl.make_desc(2, (64, 64), 4, velocity="uniform", velocity_params=[0.1, 0.2])
+    sw = sl.make_desc(2, (64, 64), 4, velocity="nlsw", velocity_params=[250.0])
+    assert sl.sl_grid_workspace_bytes(sw) >= sl.sl_grid_workspace_bytes(base) + 3 * 64 * 64 * 4
 
 
 def test_create_rejects_bad_workspace_without_gpu(libsl):
