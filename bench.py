@@ -210,18 +210,26 @@ def run_reference(args):
 
 
 def kernel_only(args):
-    """Launch only sl_remap_fields or sl_step (FP32 production path) on the swirl workload (or
-    sl_remap_fields on the 3-D deformation flow), for profilers; prints the mean CUDA-event time
-    per call."""
+    """Launch only sl_remap_fields or sl_step (FP32 production path) on the swirl workload (Z1, or
+    Z2 for remap_z2), sl_remap_fields on the 3-D deformation flow, or sl_step on the Kelvin wave
+    (nlsw), for profilers; prints the mean CUDA-event time per call."""
     import torch
     from paper_1410_2817_gb300 import build, inputs, sl
     build.build()
-    wl = inputs.workload_deform3d(args.n) if args.mode == "remap3d" else inputs.workload_swirl(args.n)
+    if args.mode == "remap3d":
+        wl = inputs.workload_deform3d(args.n)
+    elif args.mode == "nlsw":
+        wl = inputs.workload_kelvin(args.n)
+    else:
+        wl = inputs.workload_swirl(args.n)
+        if args.mode == "remap_z2":
+            wl.max_order = 2
     g = sl.grid_for(wl, sl.SL_F32)
     f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
     out = torch.empty_like(f)
-    g.advect(0.5, wl.dt)
-    remap = args.mode in ("remap", "remap3d")
+    if args.mode != "nlsw":
+        g.advect(0.5, wl.dt)
+    remap = args.mode in ("remap", "remap3d", "remap_z2")
     for _ in range(args.warmup):
         g.remap(f, out) if remap else g.step(f, out, 0.5, wl.dt, 1)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -455,7 +463,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, 3-D and serving legs")
     ap.add_argument("--serve-jobs", type=int, default=300, help="jobs of the served trace (0: skip)")
-    ap.add_argument("--mode", default="full", choices=["full", "remap", "step", "remap3d"],
+    ap.add_argument("--mode", default="full", choices=["full", "remap", "step", "remap3d", "remap_z2", "nlsw"],
                     help="remap/step: only launch that call --steps times (for profilers); prints its timing")
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
     args = ap.parse_args()

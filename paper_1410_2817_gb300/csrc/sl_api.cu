@@ -135,9 +135,9 @@ static Layout layout_of(const sl_grid_desc *d)
     off += align256((size_t)N * ds * ts);
     L.D1 = off;
     off += align256((size_t)N * ds * ts);
-    // shallow water: the RK3 registers of h, u1, u2 (three planes)
+    // shallow water: two sets of RK3 registers of h, u1, u2 and of the displacement (10 planes)
     L.rk = off;
-    if (d->velocity_kind == SL_VEL_NLSW) off += align256((size_t)N * 3 * ts);
+    if (d->velocity_kind == SL_VEL_NLSW) off += align256((size_t)N * 10 * ts);
     L.total = off;
     return L;
 }
@@ -330,13 +330,14 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
     }
     cudaError_t e = cudaSuccess;
     if (g->nlsw) {
-        // three RK3 stages on the nodes (node values in the scratch planes), then the remap back
-        // into the caller's planes: the result lands in `fields` after every step
+        // the three RK3 stages on the nodes (four launches; the node values end in the scratch
+        // planes), then the remap back into the caller's planes: the result lands in `fields`
+        // after every step
         g->d_cached = 0;
         g->next_valid = 0;
         for (int k = 0; k < nsteps; ++k) {
             e = counted(g, Launch<T>::nlsw_stages(g, (const void *const *)fields, scratch, g->D[g->dcur],
-                                                  g->D[g->dcur ^ 1], dt, s), 6);
+                                                  g->D[g->dcur ^ 1], dt, s), 4);
             if (e == cudaSuccess) e = remap_impl<T>(g, g->D[g->dcur], (const void *const *)scratch, fields, nullptr, s);
             if (e != cudaSuccess) return e;
         }

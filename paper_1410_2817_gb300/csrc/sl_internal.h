@@ -38,7 +38,8 @@ struct sl_grid {
     // A carried velocity (SL_VEL_CARRIED) lives in field planes vel_field[a] of the fields.
     int carried;
     int vel_field[3];
-    // Shallow water (SL_VEL_NLSW): the RK3 registers of h, u1, u2 (three planes in the workspace).
+    // Shallow water (SL_VEL_NLSW): two sets of RK3 registers of h, u1, u2 and of the displacement
+    // (ten planes in the workspace).
     int nlsw;
     void *rk;
 };
@@ -51,8 +52,9 @@ struct Launch {
     static cudaError_t advect(const sl_grid *g, void *D, double t, double dt, cudaStream_t s);
     static cudaError_t advect_carried(const sl_grid *g, const void *const *fields, void *D, double dt, cudaStream_t s);
     // shallow water (sl_nlsw.cu): the three RK3 stages of one step on the nodes -- node values
-    // from `fields` into `nodes`, displacement (cells) into D, its RK register into Dq; 6 launches
-    static cudaError_t nlsw_stages(const sl_grid *g, const void *const *fields, void *const *nodes, void *D, void *Dq,
+    // from `fields` into `nodes` (`fields` is overwritten), displacement (cells) into D, Dalt as
+    // scratch; 4 launches
+    static cudaError_t nlsw_stages(const sl_grid *g, const void *const *fields, void *const *nodes, void *D, void *Dalt,
                                    double dt, cudaStream_t s);
     static cudaError_t flags(const sl_grid *g, const void *const *in, uint8_t *flags, cudaStream_t s);
     static cudaError_t remap_generic(const sl_grid *g, const void *D, const uint8_t *flags, const void *const *in,

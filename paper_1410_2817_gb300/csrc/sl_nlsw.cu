@@ -7,10 +7,13 @@
 // node positions; each node moves with its own current velocity.  The remap that follows is the
 // library's ordinary one.
 //
-// One stage is two launches: the right-hand side (a stencil over the node values, so it cannot
-// update them in place) folded into the RK registers q <- A q + dt S, then the pointwise update
-// W <- W + B q of the node values and of the displacement.  The displacement is kept in cell units,
-// interleaved per node: after the third stage it is the remap's D.
+// A step is four launches.  The first computes the sources of the input fields into the RK
+// registers, q <- dt S(W_0); each of the next two forms the node values of its stage on the fly,
+// W_k = W_{k-1} + B_{k-1} q at every point of its stencil, writes them out and folds its own sources
+// in, q <- A_k q + dt S(W_k) (the registers and node values alternate between two buffers, since a
+// stencil kernel cannot update what its neighbours still read); the last applies W_3 = W_2 + B_2 q.
+// The displacement (cell units, interleaved per node) and its register follow the same pattern;
+// after the last launch it is the remap's D.
 #include <math.h>
 #include <string.h>
 
@@ -19,18 +22,6 @@
 #include "sl_internal.h"
 
 namespace {
-
-template <typename T>
-struct NlswArgs {
-    int n0, n1;
-    long long N;
-    const T *w[3];   // node values h, u1, u2 (the step's input fields at the first stage)
-    T *q[3];         // RK registers of h, u1, u2
-    T *D, *Dq;       // displacement and its RK register, cells, 2 per node
-    T A, dt, f0, lo1, dx1;
-    T inv_dx0, inv_dx1;  // 1 / dx_a (physical derivative = lattice difference / dx_a)
-    T r01, r10;          // dx0 / dx1 and dx1 / dx0 (the Jacobian in cell units)
-};
 
 template <typename T2, typename T>
 __device__ __forceinline__ T2 make_t2(T x, T y)
@@ -41,6 +32,13 @@ __device__ __forceinline__ T2 make_t2(T x, T y)
     return r;
 }
 
+// rounded products that the compiler may not fuse into a following subtraction: the displacement
+// of stage 1 is a pure product B dq, and a difference of two such products contracted to
+// fma(B, dq1, -B dq2) would leave the rounding residual of the second (a spurious ~1e-20 slope
+// of a displacement that is constant along the axis)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // lattice difference along one axis from the values at offsets -2 .. +2 (cell units)
 template <typename T, bool FD4>
 __device__ __forceinline__ T lat(T m2, T m1, T p1, T p2)
@@ -49,10 +47,29 @@ __device__ __forceinline__ T lat(T m2, T m1, T p1, T p2)
     return T(0.5) * (p1 - m1);
 }
 
-// Right-hand side of stage k at node i folded into the RK registers.  FIRST: the nodes sit on the
-// reference grid (D = 0, J = I) and the registers start from zero.
-template <typename T, bool FD4, bool FIRST>
-__global__ void __launch_bounds__(256) nlsw_rhs_kernel(const NlswArgs<T> a)
+template <typename T>
+struct NlswStage {
+    int n0, n1, nfields;
+    long long N;
+    const T *wp[SL_MAX_FIELDS];  // node values of the previous stage (the input fields at stage 0)
+    const T *qp[3];              // RK registers of the previous stage (unused at stage 0)
+    const T *ep, *dqp;           // displacement and its register, previous stage (cells, 2 per node)
+    T *qn[3];                    // RK registers of this stage
+    T *dqn;                      // displacement register of this stage
+    T *wn[SL_MAX_FIELDS];        // node values of this stage (stages 1, 2)
+    T *en;                       // displacement of this stage (stages 1, 2)
+    T A, Bp, dt, f0, lo1, dx1;
+    T inv_dx0, inv_dx1;  // 1 / dx_a (physical derivative = lattice difference / dx_a)
+    T r01, r10;          // dx0 / dx1 and dx1 / dx0 (the Jacobian in cell units)
+};
+
+// Stage K of the RK3 at every node.  K = 0: the node values are the input fields and the nodes
+// sit on the reference grid (D = 0, J = I).  K = 1, 2: the node values W_K = W_{K-1} + B q and
+// the displacement e_K = e_{K-1} + B Dq are formed at each stencil point (e_0 = 0), written out
+// at the node, and the sources of W_K are folded into the new registers.  Stage 1 also carries the
+// passive fields over.
+template <typename T, bool FD4, int K>
+__global__ void __launch_bounds__(256) nlsw_stage_kernel(const NlswStage<T> a)
 {
     using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N; i += (long long)gridDim.x * blockDim.x) {
@@ -63,31 +80,38 @@ __global__ void __launch_bounds__(256) nlsw_rhs_kernel(const NlswArgs<T> a)
         const long long ym1 = (long long)wrap_near(iy - 1, a.n1) * a.n0, yp1 = (long long)wrap_near(iy + 1, a.n1) * a.n0;
         const long long ym2 = FD4 ? (long long)wrap_near(iy - 2, a.n1) * a.n0 : 0;
         const long long yp2 = FD4 ? (long long)wrap_near(iy + 2, a.n1) * a.n0 : 0;
-        // lattice differences along x (X) and y (Y) of plane p
-        auto LX = [&](const T *p) {
-            return lat<T, FD4>(FD4 ? __ldg(p + r + xm2) : T(0), __ldg(p + r + xm1), __ldg(p + r + xp1),
-                               FD4 ? __ldg(p + r + xp2) : T(0));
+        // node value of field c at node o in this stage
+        auto W = [&](int c, long long o) {
+            const T w = __ldg(a.wp[c] + o);
+            return K == 0 ? w : w + a.Bp * __ldg(a.qp[c] + o);
         };
-        auto LY = [&](const T *p) {
-            return lat<T, FD4>(FD4 ? __ldg(p + ym2 + ix) : T(0), __ldg(p + ym1 + ix), __ldg(p + yp1 + ix),
-                               FD4 ? __ldg(p + yp2 + ix) : T(0));
+        // displacement at node o in this stage (cells)
+        auto E = [&](long long o) {
+            const T2 dq = reinterpret_cast<const T2 *>(a.dqp)[o];
+            if (K == 1) return make_t2<T2>(mul_rn(a.Bp, dq.x), mul_rn(a.Bp, dq.y));
+            const T2 e = reinterpret_cast<const T2 *>(a.ep)[o];
+            return make_t2<T2>(e.x + a.Bp * dq.x, e.y + a.Bp * dq.y);
         };
-        const T hX = LX(a.w[0]), hY = LY(a.w[0]);
-        const T uX = LX(a.w[1]), uY = LY(a.w[1]);
-        const T vX = LX(a.w[2]), vY = LY(a.w[2]);
+        auto LX = [&](int c) {
+            return lat<T, FD4>(FD4 ? W(c, r + xm2) : T(0), W(c, r + xm1), W(c, r + xp1), FD4 ? W(c, r + xp2) : T(0));
+        };
+        auto LY = [&](int c) {
+            return lat<T, FD4>(FD4 ? W(c, ym2 + ix) : T(0), W(c, ym1 + ix), W(c, yp1 + ix), FD4 ? W(c, yp2 + ix) : T(0));
+        };
+        const T hX = LX(0), hY = LY(0), uX = LX(1), uY = LY(1), vX = LX(2), vY = LY(2);
+        const T h = W(0, i), u = W(1, i), v = W(2, i);
         T hx, hy, div, ey = T(0);
-        if (FIRST) {
+        if (K == 0) {
             hx = hX * a.inv_dx0;
             hy = hY * a.inv_dx1;
             div = uX * a.inv_dx0 + vY * a.inv_dx1;
         } else {
-            const T2 *D2 = reinterpret_cast<const T2 *>(a.D);
-            auto eX = [&](long long o0, long long o1, long long o2, long long o3) {  // (ex, ey) differences
-                const T2 m2 = FD4 ? D2[o0] : T2(), m1 = D2[o1], p1 = D2[o2], p2 = FD4 ? D2[o3] : T2();
+            auto ED = [&](long long o0, long long o1, long long o2, long long o3) {  // (ex, ey) differences
+                const T2 m2 = FD4 ? E(o0) : T2(), m1 = E(o1), p1 = E(o2), p2 = FD4 ? E(o3) : T2();
                 return make_t2<T2>(lat<T, FD4>(m2.x, m1.x, p1.x, p2.x), lat<T, FD4>(m2.y, m1.y, p1.y, p2.y));
             };
-            const auto dX = eX(r + xm2, r + xm1, r + xp1, r + xp2);      // d(ex, ey)/dX, cells per cell
-            const auto dY = eX(ym2 + ix, ym1 + ix, yp1 + ix, yp2 + ix);  // d(ex, ey)/dY
+            const T2 dX = ED(r + xm2, r + xm1, r + xp1, r + xp2);      // d(ex, ey)/dX, cells per cell
+            const T2 dY = ED(ym2 + ix, ym1 + ix, yp1 + ix, yp2 + ix);  // d(ex, ey)/dY
             // J_ab = delta_ab + (dx_a / dx_b) d e_a / d X_b with e in cells
             const T J00 = T(1) + dX.x, J01 = dY.x * a.r01, J10 = dX.y * a.r10, J11 = T(1) + dY.y;
             const T rdet = T(1) / (J00 * J11 - J01 * J10);
@@ -96,114 +120,146 @@ __global__ void __launch_bounds__(256) nlsw_rhs_kernel(const NlswArgs<T> a)
             hx = I00 * hXp + I10 * hYp;
             hy = I01 * hXp + I11 * hYp;
             div = uX * a.inv_dx0 * I00 + uY * a.inv_dx1 * I10 + vX * a.inv_dx0 * I01 + vY * a.inv_dx1 * I11;
-            ey = D2[i].y;
+            const T2 ei = E(i);
+            ey = ei.y;
+            a.wn[0][i] = h;
+            a.wn[1][i] = u;
+            a.wn[2][i] = v;
+            reinterpret_cast<T2 *>(a.en)[i] = ei;
+            if (K == 1)
+                for (int c = 3; c < a.nfields; ++c) a.wn[c][i] = __ldg(a.wp[c] + i);
         }
-        const T h = __ldg(a.w[0] + i), u = __ldg(a.w[1] + i), v = __ldg(a.w[2] + i);
         const T f = a.f0 * (a.lo1 + (T(iy) + ey) * a.dx1);
         const T S0 = -(T(1) + h) * div, S1 = -hx + f * v, S2 = -hy - f * u;
-        if (FIRST) {
-            a.q[0][i] = a.dt * S0;
-            a.q[1][i] = a.dt * S1;
-            a.q[2][i] = a.dt * S2;
-            reinterpret_cast<T2 *>(a.Dq)[i] = make_t2<T2>(a.dt * u * a.inv_dx0, a.dt * v * a.inv_dx1);
+        const T du = a.dt * u * a.inv_dx0, dv = a.dt * v * a.inv_dx1;
+        if (K == 0) {
+            a.qn[0][i] = a.dt * S0;
+            a.qn[1][i] = a.dt * S1;
+            a.qn[2][i] = a.dt * S2;
+            reinterpret_cast<T2 *>(a.dqn)[i] = make_t2<T2>(du, dv);
         } else {
-            a.q[0][i] = a.A * a.q[0][i] + a.dt * S0;
-            a.q[1][i] = a.A * a.q[1][i] + a.dt * S1;
-            a.q[2][i] = a.A * a.q[2][i] + a.dt * S2;
-            const T2 dq = reinterpret_cast<const T2 *>(a.Dq)[i];
-            reinterpret_cast<T2 *>(a.Dq)[i] =
-                make_t2<T2>(a.A * dq.x + a.dt * u * a.inv_dx0, a.A * dq.y + a.dt * v * a.inv_dx1);
+            a.qn[0][i] = a.A * __ldg(a.qp[0] + i) + a.dt * S0;
+            a.qn[1][i] = a.A * __ldg(a.qp[1] + i) + a.dt * S1;
+            a.qn[2][i] = a.A * __ldg(a.qp[2] + i) + a.dt * S2;
+            const T2 dq = reinterpret_cast<const T2 *>(a.dqp)[i];
+            reinterpret_cast<T2 *>(a.dqn)[i] = make_t2<T2>(a.A * dq.x + du, a.A * dq.y + dv);
         }
     }
 }
 
 template <typename T>
-struct NlswUpdate {
+struct NlswFinal {
     long long N;
-    int nfields;
-    const T *src[SL_MAX_FIELDS];  // the step's input fields (first stage) or the node values
-    T *dst[SL_MAX_FIELDS];        // the node values
-    const T *q[3];
-    T *D;
-    const T *Dq;
+    const T *w[3], *q[3], *dq;
+    T *out[3];
+    T *D;  // e_2 in, the step's displacement out (cells, 2 per node)
     T B;
 };
 
-// W <- W + B q for h, u1, u2 and D <- D + B Dq; FIRST: W and D start from the input fields and 0
-// (passive fields are copied).
-template <typename T, bool FIRST>
-__global__ void __launch_bounds__(256) nlsw_update_kernel(const NlswUpdate<T> a)
+// W_3 = W_2 + B_2 q and D = e_2 + B_2 Dq (pointwise; D in place)
+template <typename T>
+__global__ void __launch_bounds__(256) nlsw_final_kernel(const NlswFinal<T> a)
 {
     using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N; i += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a.dst[c][i] = a.src[c][i] + a.B * a.q[c][i];
-        if (FIRST)
-            for (int c = 3; c < a.nfields; ++c) a.dst[c][i] = a.src[c][i];
-        const T2 dq = reinterpret_cast<const T2 *>(a.Dq)[i];
-        T2 d = FIRST ? make_t2<T2>(T(0), T(0)) : reinterpret_cast<const T2 *>(a.D)[i];
+        for (int c = 0; c < 3; ++c) a.out[c][i] = a.w[c][i] + a.B * a.q[c][i];
+        const T2 dq = reinterpret_cast<const T2 *>(a.dq)[i];
+        T2 d = reinterpret_cast<T2 *>(a.D)[i];
         d.x += a.B * dq.x;
         d.y += a.B * dq.y;
         reinterpret_cast<T2 *>(a.D)[i] = d;
     }
 }
 
+template <typename T, int K>
+cudaError_t launch_stage(bool fd4, int blocks, const NlswStage<T> &a, cudaStream_t s)
+{
+    if (fd4)
+        nlsw_stage_kernel<T, true, K><<<blocks, 256, 0, s>>>(a);
+    else
+        nlsw_stage_kernel<T, false, K><<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+// Buffers: F = the caller's fields (input; W_2 after stage 2), S = the scratch planes (W_1, then
+// W_3 and the passive fields: the remap's input), registers qA/qB (3 planes each) and DqA/DqB (2
+// per node) in the grid's workspace, e_1 in Dalt, e_2 and the final displacement in D.
 template <typename T>
-cudaError_t Launch<T>::nlsw_stages(const sl_grid *g, const void *const *fields, void *const *nodes, void *D, void *Dq,
+cudaError_t Launch<T>::nlsw_stages(const sl_grid *g, const void *const *fields, void *const *nodes, void *D, void *Dalt,
                                    double dt, cudaStream_t s)
 {
     const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0}, B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
     const long long N = g->N;
     T *rk = (T *)g->rk;
-    NlswArgs<T> ra;
-    memset(&ra, 0, sizeof(ra));
-    ra.n0 = (int)g->n[0];
-    ra.n1 = (int)g->n[1];
-    ra.N = N;
-    for (int c = 0; c < 3; ++c) ra.q[c] = rk + (long long)c * N;
-    ra.D = (T *)D;
-    ra.Dq = (T *)Dq;
-    ra.dt = (T)dt;
-    ra.f0 = (T)g->vel_params[0];
-    ra.lo1 = (T)g->desc.lo[1];
-    ra.dx1 = (T)g->dx[1];
-    ra.inv_dx0 = (T)(1.0 / g->dx[0]);
-    ra.inv_dx1 = (T)(1.0 / g->dx[1]);
-    ra.r01 = (T)(g->dx[0] / g->dx[1]);
-    ra.r10 = (T)(g->dx[1] / g->dx[0]);
-    NlswUpdate<T> ua;
-    memset(&ua, 0, sizeof(ua));
-    ua.N = N;
-    ua.nfields = g->nfields;
-    for (int c = 0; c < g->nfields; ++c) ua.dst[c] = (T *)nodes[c];
-    for (int c = 0; c < 3; ++c) ua.q[c] = rk + (long long)c * N;
-    ua.D = (T *)D;
-    ua.Dq = (const T *)Dq;
+    T *qA[3] = {rk, rk + N, rk + 2 * N}, *qB[3] = {rk + 3 * N, rk + 4 * N, rk + 5 * N};
+    T *DqA = rk + 6 * N, *DqB = rk + 8 * N;
+    NlswStage<T> a;
+    memset(&a, 0, sizeof(a));
+    a.n0 = (int)g->n[0];
+    a.n1 = (int)g->n[1];
+    a.nfields = g->nfields;
+    a.N = N;
+    a.dt = (T)dt;
+    a.f0 = (T)g->vel_params[0];
+    a.lo1 = (T)g->desc.lo[1];
+    a.dx1 = (T)g->dx[1];
+    a.inv_dx0 = (T)(1.0 / g->dx[0]);
+    a.inv_dx1 = (T)(1.0 / g->dx[1]);
+    a.r01 = (T)(g->dx[0] / g->dx[1]);
+    a.r10 = (T)(g->dx[1] / g->dx[0]);
     const bool fd4 = g->desc.max_order >= 2;
     const int blocks = grid_stride_blocks(g, N, 256);
-    for (int k = 0; k < 3; ++k) {
-        const bool first = k == 0;
-        for (int c = 0; c < 3; ++c) ra.w[c] = (const T *)(first ? fields[c] : nodes[c]);
-        ra.A = (T)A[k];
-        if (first) {
-            if (fd4) nlsw_rhs_kernel<T, true, true><<<blocks, 256, 0, s>>>(ra);
-            else nlsw_rhs_kernel<T, false, true><<<blocks, 256, 0, s>>>(ra);
-        } else {
-            if (fd4) nlsw_rhs_kernel<T, true, false><<<blocks, 256, 0, s>>>(ra);
-            else nlsw_rhs_kernel<T, false, false><<<blocks, 256, 0, s>>>(ra);
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        for (int c = 0; c < g->nfields; ++c) ua.src[c] = (const T *)(first ? fields[c] : nodes[c]);
-        ua.B = (T)B[k];
-        if (first) nlsw_update_kernel<T, true><<<blocks, 256, 0, s>>>(ua);
-        else nlsw_update_kernel<T, false><<<blocks, 256, 0, s>>>(ua);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+    // stage 0: sources of the input fields
+    for (int c = 0; c < g->nfields; ++c) a.wp[c] = (const T *)fields[c];
+    for (int c = 0; c < 3; ++c) a.qn[c] = qA[c];
+    a.dqn = DqA;
+    cudaError_t e = launch_stage<T, 0>(fd4, blocks, a, s);
+    if (e != cudaSuccess) return e;
+    // stage 1: W_1 = F + B_0 qA into S (passive fields copied), e_1 into Dalt; registers into qB
+    for (int c = 0; c < 3; ++c) {
+        a.qp[c] = qA[c];
+        a.qn[c] = qB[c];
     }
-    return cudaSuccess;
+    for (int c = 0; c < g->nfields; ++c) a.wn[c] = (T *)nodes[c];
+    a.dqp = DqA;
+    a.dqn = DqB;
+    a.en = (T *)Dalt;
+    a.A = (T)A[1];
+    a.Bp = (T)B[0];
+    e = launch_stage<T, 1>(fd4, blocks, a, s);
+    if (e != cudaSuccess) return e;
+    // stage 2: W_2 = W_1 + B_1 qB into F, e_2 into D; registers into qA
+    for (int c = 0; c < 3; ++c) {
+        a.wp[c] = (const T *)nodes[c];
+        a.qp[c] = qB[c];
+        a.qn[c] = qA[c];
+        a.wn[c] = (T *)fields[c];
+    }
+    a.ep = (const T *)Dalt;
+    a.dqp = DqB;
+    a.dqn = DqA;
+    a.en = (T *)D;
+    a.A = (T)A[2];
+    a.Bp = (T)B[1];
+    e = launch_stage<T, 2>(fd4, blocks, a, s);
+    if (e != cudaSuccess) return e;
+    // W_3 = W_2 + B_2 qA into S, D = e_2 + B_2 DqA
+    NlswFinal<T> fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.N = N;
+    for (int c = 0; c < 3; ++c) {
+        fa.w[c] = (const T *)fields[c];
+        fa.q[c] = qA[c];
+        fa.out[c] = (T *)nodes[c];
+    }
+    fa.dq = DqA;
+    fa.D = (T *)D;
+    fa.B = (T)B[2];
+    nlsw_final_kernel<T><<<blocks, 256, 0, s>>>(fa);
+    return cudaGetLastError();
 }
 
 template cudaError_t Launch<float>::nlsw_stages(const sl_grid *, const void *const *, void *const *, void *, void *,

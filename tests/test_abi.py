@@ -75,10 +75,10 @@ def test_workspace_bytes_and_validation(libsl):
                sl.make_desc(3, (8, 8, 8), 3, velocity="carried", velocity_params=[]),
                sl.make_desc(2, (64, 64), 4, velocity="nlsw", velocity_params=[250.0])):
         assert sl.sl_grid_workspace_bytes(ok) > 0
-    # shallow-water grids also hold the RK3 registers of h, u1, u2
+    # shallow-water grids also hold two sets of RK3 registers (h, u1, u2 and the displacement)
     base = sl.make_desc(2, (64, 64), 4, velocity="uniform", velocity_params=[0.1, 0.2])
     sw = sl.make_desc(2, (64, 64), 4, velocity="nlsw", velocity_params=[250.0])
-    assert sl.sl_grid_workspace_bytes(sw) >= sl.sl_grid_workspace_bytes(base) + 3 * 64 * 64 * 4
+    assert sl.sl_grid_workspace_bytes(sw) >= sl.sl_grid_workspace_bytes(base) + 10 * 64 * 64 * 4
 
 
 def test_create_rejects_bad_workspace_without_gpu(libsl):

@@ -225,3 +225,42 @@ def test_fused_tiled_step_matches_plain_f32(sl):
     l0 = gt.diagnostics()["kernel_launches"]
     gt.step(f, torch.empty_like(f), 0.0, wl.dt, 6)
     assert gt.diagnostics()["kernel_launches"] - l0 == 1 + 6
+
+
+@pytest.mark.parametrize("n", [(4, 4), (6, 5), (1 << 20, 4)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_extreme_sides(sl, orc, n, dtype):
+    """Sides down to 4 (the six-point stencil wraps more than once round the period) and 2^20:
+    FP64 within 1e-12 of the oracle, FP32 (tiled, global path for windows wider than the grid)
+    to FP32 accuracy, limiter on for FP64 and off for FP32."""
+    n0, n1 = n
+    D = inputs.smooth_displacement(n, amplitude=0.3, seed=17, shift=(1.3, -0.6))
+    rng = np.random.default_rng(18)
+    x = np.arange(n0) / n0
+    h = np.stack([np.tile(np.sin(2 * np.pi * x) + 0.3 * np.cos(6 * np.pi * x), (n1, 1)),
+                  (rng.uniform(size=(n1, n0)) > 0.6) * 1.0])
+    thr = 0.25 if dtype == "f64" else -1.0
+    og = orc.OracleGrid(dim=2, n=n, nfields=2, max_order=2, threshold=thr, start=orc.START_BACKWARD)
+    fl = orc.flags(og, h)
+    sd, td = (sl.SL_F64, torch.float64) if dtype == "f64" else (sl.SL_F32, torch.float32)
+    g = sl.Grid(2, n, 2, sd, max_order=2, limiter_threshold=thr, walk_start=sl.SL_START_BACKWARD)
+    g.set_displacement(torch.tensor(D, dtype=td, device=DEV))
+    hin = torch.tensor(h, dtype=td, device=DEV)
+    hout = torch.empty_like(hin)
+    g.remap(hin, hout)
+    torch.cuda.synchronize()
+    got = hout.double().cpu().numpy()
+    assert sum(g.diagnostics()[k] for k in ("fail_locate", "fail_newton", "fail_fold")) == 0
+    rng2 = np.random.default_rng(19)
+    idx = [(a, b) for a in range(n0) for b in range(n1)] if n0 * n1 <= 64 else \
+        list(zip(rng2.integers(0, n0, 300), rng2.integers(0, n1, 300)))
+    for (jx, jy) in idx:
+        c, xi, st, _, _ = orc.locate(og, D, (int(jx), int(jy)))
+        assert st == orc.OK
+        for q in range(2):
+            v = orc.interp(og, h[q], c, xi, orc.order(og, fl, c, q))
+            if dtype == "f64":
+                if not np.any(np.minimum(np.abs(xi), np.abs(1 - xi)) < TIE):
+                    assert abs(got[q, jy, jx] - v) <= 1e-12 * max(1.0, abs(v)), (jx, jy, q)
+            else:
+                assert abs(got[q, jy, jx] - v) <= 2e-5 * max(1.0, abs(v)), (jx, jy, q, got[q, jy, jx], v)
