@@ -648,9 +648,12 @@ int or_eval_in_element(const or_grid *g, const double *D, const uint8_t *flags, 
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* Sec. 3.3, eq. (nlsw), nu = 0: the non-dimensional shallow-water system on the moving nodes,    */
-/*   Dh/Dt = -(1 + h) div u,   Du/Dt = -grad h - f u_perp,   u_perp = (-u2, u1),  f = f0 x2,      */
-/* with h, u1, u2 the fields 0, 1, 2 (further fields are passive) and vel_params = (f0).          */
+/* Sec. 3.3, eq. (nlsw): the non-dimensional shallow-water system on the moving nodes,            */
+/*   Dh/Dt = -(1 + h) div u,                                                                       */
+/*   Du/Dt = -grad h - f u_perp + nu div[(1 + h)(grad u + grad u^T)],  u_perp = (-u2, u1), f = f0 x2, */
+/* with h, u1, u2 the fields 0, 1, 2 (further fields are passive), vel_params = (f0) or (f0, nu). */
+/* The viscous term takes two passes per stage: the stress tau = (1 + h)(grad u + grad u^T) at    */
+/* every node, then its divergence by the same differences.                                       */
 /* Sec. 2: spatial derivatives by finite differences on the reference grid, time by Williamson's */
 /* low-storage RK3 over the step, then the reset (remap).  Readings: the step starts with the    */
 /* nodes on the reference grid and remaps once; at every stage the derivatives are taken on the */
@@ -680,12 +683,27 @@ static double lattice_derivative(const or_grid *g, const double *w, const int64_
 /* One step of the shallow-water system: h (nfields planes) is replaced by the remapped fields.
  * Scratch: W (nfields planes), q (3 planes), e and qx (2 planes each), D (2 per node),
  * flags (N), tmp (nfields planes).  Returns the failed targets of the remap. */
+/* Jacobian J = dx/dX of the node positions at node k (e: displacement planes, physical units)
+ * and its inverse, row-major I[0..3] = (J^-1)_00, _01, _10, _11. */
+static void node_jacobian_inverse(const or_grid *g, const double *ex, const double *ey, const int64_t k[3],
+                                  const double dx[2], double I[4])
+{
+    const double J00 = 1.0 + lattice_derivative(g, ex, k, 0, dx[0]), J01 = lattice_derivative(g, ex, k, 1, dx[1]);
+    const double J10 = lattice_derivative(g, ey, k, 0, dx[0]), J11 = 1.0 + lattice_derivative(g, ey, k, 1, dx[1]);
+    const double det = J00 * J11 - J01 * J10;
+    I[0] = J11 / det;
+    I[1] = -J01 / det;
+    I[2] = -J10 / det;
+    I[3] = J00 / det;
+}
+
 static int64_t or_nlsw_step(const or_grid *g, double *h, double dt, double *W, double *q, double *e, double *qx,
-                            double *D, uint8_t *flags, double *tmp)
+                            double *tau, double *D, uint8_t *flags, double *tmp)
 {
     const int64_t N = total_nodes(g);
     const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0}, B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
     const double f0 = g->vel_params[0];
+    const double nu = g->n_vel_params > 1 ? g->vel_params[1] : 0.0;
     double dx[2];
     for (int a = 0; a < 2; ++a) dx[a] = (g->hi[a] - g->lo[a]) / (double)g->n[a];
     memcpy(W, h, sizeof(double) * (size_t)N * (size_t)g->nfields);
@@ -696,15 +714,32 @@ static int64_t or_nlsw_step(const or_grid *g, double *h, double dt, double *W, d
     double *ex = e, *ey = e + N; /* node displacement (physical units), one plane per axis */
     set_threads(g);
     for (int s = 0; s < 3; ++s) {
+        if (nu != 0.0) {
+            /* pass 1: the stress tau = (1 + h)(grad u + grad u^T) at every node (three planes) */
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < N; ++i) {
+                int64_t k[3];
+                node_coords(g, i, k);
+                double I[4];
+                node_jacobian_inverse(g, ex, ey, k, dx, I);
+                const double uX = lattice_derivative(g, wu, k, 0, dx[0]), uY = lattice_derivative(g, wu, k, 1, dx[1]);
+                const double vX = lattice_derivative(g, wv, k, 0, dx[0]), vY = lattice_derivative(g, wv, k, 1, dx[1]);
+                const double ux = I[0] * uX + I[2] * uY, uy = I[1] * uX + I[3] * uY;
+                const double vx = I[0] * vX + I[2] * vY, vy = I[1] * vX + I[3] * vY;
+                const double d = 1.0 + wh[i];
+                tau[i] = d * 2.0 * ux;
+                tau[N + i] = d * (uy + vx);
+                tau[2 * N + i] = d * 2.0 * vy;
+            }
+        }
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             int64_t k[3];
             node_coords(g, i, k);
             /* Jacobian of the node positions and its inverse */
-            const double J00 = 1.0 + lattice_derivative(g, ex, k, 0, dx[0]), J01 = lattice_derivative(g, ex, k, 1, dx[1]);
-            const double J10 = lattice_derivative(g, ey, k, 0, dx[0]), J11 = 1.0 + lattice_derivative(g, ey, k, 1, dx[1]);
-            const double det = J00 * J11 - J01 * J10;
-            const double I00 = J11 / det, I01 = -J01 / det, I10 = -J10 / det, I11 = J00 / det;
+            double I[4];
+            node_jacobian_inverse(g, ex, ey, k, dx, I);
+            const double I00 = I[0], I01 = I[1], I10 = I[2], I11 = I[3];
             /* reference-coordinate derivatives */
             const double hX = lattice_derivative(g, wh, k, 0, dx[0]), hY = lattice_derivative(g, wh, k, 1, dx[1]);
             const double uX = lattice_derivative(g, wu, k, 0, dx[0]), uY = lattice_derivative(g, wu, k, 1, dx[1]);
@@ -714,7 +749,18 @@ static int64_t or_nlsw_step(const or_grid *g, double *h, double dt, double *W, d
             const double div = uX * I00 + uY * I10 + vX * I01 + vY * I11;
             const double y = g->lo[1] + (double)k[1] * dx[1] + ey[i];
             const double f = f0 * y;
-            const double S[3] = {-(1.0 + wh[i]) * div, -hx + f * wv[i], -hy - f * wu[i]};
+            double S[3] = {-(1.0 + wh[i]) * div, -hx + f * wv[i], -hy - f * wu[i]};
+            if (nu != 0.0) {
+                /* pass 2: nu div tau, (div tau)_a = d tau_a0 / dx + d tau_a1 / dy */
+                const double *t11 = tau, *t12 = tau + N, *t22 = tau + 2 * N;
+                const double aX = lattice_derivative(g, t11, k, 0, dx[0]), aY = lattice_derivative(g, t11, k, 1, dx[1]);
+                const double bX = lattice_derivative(g, t12, k, 0, dx[0]), bY = lattice_derivative(g, t12, k, 1, dx[1]);
+                const double cX = lattice_derivative(g, t22, k, 0, dx[0]), cY = lattice_derivative(g, t22, k, 1, dx[1]);
+                const double t11x = I00 * aX + I10 * aY, t12y = I01 * bX + I11 * bY;
+                const double t12x = I00 * bX + I10 * bY, t22y = I01 * cX + I11 * cY;
+                S[1] += nu * (t11x + t12y);
+                S[2] += nu * (t12x + t22y);
+            }
             for (int c = 0; c < 3; ++c) q[(int64_t)c * N + i] = A[s] * q[(int64_t)c * N + i] + dt * S[c];
             qx[i] = A[s] * qx[i] + dt * wu[i];
             qx[N + i] = A[s] * qx[N + i] + dt * wv[i];
@@ -743,13 +789,15 @@ static int64_t or_nlsw_steps(const or_grid *g, double *h, double dt, int nsteps)
     double *q = (double *)malloc(sizeof(double) * (size_t)N * 3);
     double *e = (double *)malloc(sizeof(double) * (size_t)N * 2), *qx = (double *)malloc(sizeof(double) * (size_t)N * 2);
     double *D = (double *)malloc(sizeof(double) * (size_t)N * 2);
+    double *tau = (double *)malloc(sizeof(double) * (size_t)N * 3);
     uint8_t *flags = (uint8_t *)malloc((size_t)N);
     int64_t nfail = 0;
-    if (W && tmp && q && e && qx && D && flags) {
-        for (int s = 0; s < nsteps; ++s) nfail += or_nlsw_step(g, h, dt, W, q, e, qx, D, flags, tmp);
+    if (W && tmp && q && e && qx && D && tau && flags) {
+        for (int s = 0; s < nsteps; ++s) nfail += or_nlsw_step(g, h, dt, W, q, e, qx, tau, D, flags, tmp);
     } else {
         nfail = -1;
     }
+    free(tau);
     free(W);
     free(tmp);
     free(q);

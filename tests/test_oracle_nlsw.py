@@ -138,3 +138,45 @@ def test_uniform_stream_moves_a_tracer_like_the_uniform_flow(orc):
     assert np.abs(out[0]).max() <= 1e-15 and np.abs(out[1] - 0.3).max() <= 1e-15
     rest, _ = _run(orc, _nlsw_grid(orc, (16, 16), 2), np.zeros((3, 16, 16)), 0.01, 4)
     assert np.abs(rest).max() == 0.0
+
+
+@pytest.mark.parametrize("orient", ["u1_of_x2", "u2_of_x1"])
+@pytest.mark.parametrize("max_order,min_rate,max_err", [(2, 3.5, 3e-6), (1, 1.8, 1e-3)])
+def test_viscous_shear_decays(orc, orient, max_order, min_rate, max_err):
+    """nu = 0.01, h = 0, f0 = 0, a shear wave u1 = A sin(2 pi x2) (or u2 = A sin(2 pi x1)): the
+    advection and pressure terms vanish and the wave decays as exp(-nu (2 pi)^2 t) (eq. nlsw's
+    viscous term reduces to nu times the Laplacian); rates measured 4.0 (Z2) and 2.0 (Z1)."""
+    nu, amp, T = 0.01, 0.05, 0.5
+    errs = []
+    for n in (32, 64):
+        steps = int(round(T / (0.5 / n)))
+        x = np.arange(n) / n
+        X1, X2 = np.meshgrid(x, x)
+        prof = amp * np.sin(2 * np.pi * (X2 if orient == "u1_of_x2" else X1))
+        u, v = (prof, np.zeros_like(prof)) if orient == "u1_of_x2" else (np.zeros_like(prof), prof)
+        g = orc.OracleGrid(dim=2, n=(n, n), nfields=3, velocity="nlsw", velocity_params=[0.0, nu],
+                           max_order=max_order, threshold=-1.0)
+        out, nfail = _run(orc, g, np.stack([np.zeros_like(u), u, v]), T / steps, steps)
+        assert nfail == 0 and np.abs(out[0]).max() == 0.0
+        comp = out[1] if orient == "u1_of_x2" else out[2]
+        errs.append(float(np.abs(comp - np.exp(-nu * (2 * np.pi) ** 2 * T) * prof).max()) / amp)
+    assert np.log2(errs[0] / errs[1]) >= min_rate, errs
+    assert errs[1] <= max_err, errs
+
+
+def test_viscous_damped_gravity_wave(orc):
+    """f0 = 0, nu = 0.01, 1-D standing wave h = A cos(k x), u = 0 (A = 1e-4): the linearised
+    system h_t = -u_x, u_t = -h_x + 2 nu u_xx (the stress's normal component carries the factor
+    2) gives h = A cos(k x) exp(-a t) (cos w t + a / w sin w t), a = nu k^2, w^2 = k^2 - a^2.
+    Without the factor 2 the error would be ~0.1 A."""
+    n, kap, amp, nu, T = 64, 4 * np.pi, 1e-4, 0.01, 0.3
+    steps = int(round(T / (0.5 / n)))
+    x = np.arange(n) / n
+    h0 = np.tile(amp * np.cos(kap * x), (4, 1))
+    g = orc.OracleGrid(dim=2, n=(n, 4), nfields=3, velocity="nlsw", velocity_params=[0.0, nu], max_order=2,
+                       threshold=-1.0)
+    out, _ = _run(orc, g, np.stack([h0, np.zeros_like(h0), np.zeros_like(h0)]), T / steps, steps)
+    a = nu * kap ** 2
+    w = np.sqrt(kap ** 2 - a ** 2)
+    H = amp * np.exp(-a * T) * (np.cos(w * T) + a / w * np.sin(w * T))
+    assert np.abs(out[0] - H * np.cos(kap * x)[None]).max() <= 2e-4 * amp
