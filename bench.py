@@ -371,31 +371,34 @@ def quintic_leg(torch, sl, inputs, flush, steps=10):
 
 
 def nlsw_leg(torch, sl, inputs, flush, steps=10):
-    """Shallow water (Sec. 3.3) on 1024^2: the paper's Kelvin-wave test (f0 = 250, amplitude 1e-4,
-    Z2, limiter off, dt = dx / 2), FP32.  Each step is three RK3 stages on the nodes (six launches:
-    sources by fourth-order differences through the node Jacobian, then the node update) and the
-    tiled quintic remap; L2 flushed before each step."""
-    wl = inputs.workload_kelvin(N_SIDE)
-    g = sl.grid_for(wl, sl.SL_F32)
-    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
-    s = torch.empty_like(f)
-    g.step(f, s, 0.0, wl.dt, 3)
-    l0 = g.diagnostics()["kernel_launches"]
-    ev = []
-    for q in range(steps):
-        flush.fill_(q & 0xff)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.step(f, s, 0.0, wl.dt, 1)
-        b.record()
-        ev.append((a, b))
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-    d = g.diagnostics()
-    out = {"workload": f"kelvin wave {N_SIDE}^2, fields (h, u1, u2), Z2, FP32", "ms_per_step": ms,
-           "value": wl.nnodes / (ms * 1e-3), "unit": UNIT, "launches_per_step": (d["kernel_launches"] - l0) / steps,
-           "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"]}
-    g.close()
+    """Shallow water (Sec. 3.3) on 1024^2, FP32, Z2, limiter off, dt = dx / 2: the paper's linear
+    Kelvin-wave test (f0 = 250, amplitude 1e-4; three RK3 stages in four launches and the tiled
+    quintic remap) and its nonlinear run (amplitude 0.5, viscosity 0.0005: a stress pass before
+    each stage, seven stage launches).  L2 flushed before each step."""
+    out = {}
+    for name, amp, nu in (("linear", 1e-4, 0.0), ("nonlinear_viscous", 0.5, 0.0005)):
+        wl = inputs.workload_kelvin(N_SIDE, amp=amp, nu=nu)
+        g = sl.grid_for(wl, sl.SL_F32)
+        f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+        s = torch.empty_like(f)
+        g.step(f, s, 0.0, wl.dt, 3)
+        l0 = g.diagnostics()["kernel_launches"]
+        ev = []
+        for q in range(steps):
+            flush.fill_(q & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.step(f, s, 0.0, wl.dt, 1)
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        d = g.diagnostics()
+        out[name] = {"workload": f"kelvin wave {N_SIDE}^2, amplitude {amp}, nu {nu}, fields (h, u1, u2), Z2, FP32",
+                     "ms_per_step": ms, "value": wl.nnodes / (ms * 1e-3), "unit": UNIT,
+                     "launches_per_step": (d["kernel_launches"] - l0) / steps,
+                     "failed_targets": d["fail_locate"] + d["fail_newton"] + d["fail_fold"]}
+        g.close()
     return out
 
 

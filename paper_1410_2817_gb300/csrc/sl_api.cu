@@ -97,7 +97,8 @@ static const char *check_desc(const sl_grid_desc *d)
     }
     case SL_VEL_NLSW:
         if (d->dim != 2 || d->nfields < 3) return "nlsw is 2-D with at least 3 fields (h, u1, u2)";
-        if (np != 1) return "nlsw takes one parameter (f0)";
+        if (np != 1 && np != 2) return "nlsw takes f0 and optionally the viscosity nu";
+        if (np == 2 && !(p[1] >= 0.0)) return "nlsw viscosity must be >= 0";
         if (d->integrator != SL_WRK3 || d->trajectory_substeps > 1)
             return "nlsw integrates with SL_WRK3, one step per remap";
         break;
@@ -135,9 +136,10 @@ static Layout layout_of(const sl_grid_desc *d)
     off += align256((size_t)N * ds * ts);
     L.D1 = off;
     off += align256((size_t)N * ds * ts);
-    // shallow water: two sets of RK3 registers of h, u1, u2 and of the displacement (10 planes)
+    // shallow water: two sets of RK3 registers of h, u1, u2 and of the displacement, and the
+    // viscous stress (13 planes)
     L.rk = off;
-    if (d->velocity_kind == SL_VEL_NLSW) off += align256((size_t)N * 10 * ts);
+    if (d->velocity_kind == SL_VEL_NLSW) off += align256((size_t)N * 13 * ts);
     L.total = off;
     return L;
 }
@@ -337,7 +339,7 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
         g->next_valid = 0;
         for (int k = 0; k < nsteps; ++k) {
             e = counted(g, Launch<T>::nlsw_stages(g, (const void *const *)fields, scratch, g->D[g->dcur],
-                                                  g->D[g->dcur ^ 1], dt, s), 4);
+                                                  g->D[g->dcur ^ 1], dt, s), nlsw_kernels_per_step(g));
             if (e == cudaSuccess) e = remap_impl<T>(g, g->D[g->dcur], (const void *const *)scratch, fields, nullptr, s);
             if (e != cudaSuccess) return e;
         }

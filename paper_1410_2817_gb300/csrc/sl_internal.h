@@ -38,8 +38,8 @@ struct sl_grid {
     // A carried velocity (SL_VEL_CARRIED) lives in field planes vel_field[a] of the fields.
     int carried;
     int vel_field[3];
-    // Shallow water (SL_VEL_NLSW): two sets of RK3 registers of h, u1, u2 and of the displacement
-    // (ten planes in the workspace).
+    // Shallow water (SL_VEL_NLSW): two sets of RK3 registers of h, u1, u2 and of the displacement,
+    // and the viscous stress (thirteen planes in the workspace).
     int nlsw;
     void *rk;
 };
@@ -53,7 +53,7 @@ struct Launch {
     static cudaError_t advect_carried(const sl_grid *g, const void *const *fields, void *D, double dt, cudaStream_t s);
     // shallow water (sl_nlsw.cu): the three RK3 stages of one step on the nodes -- node values
     // from `fields` into `nodes` (`fields` is overwritten), displacement (cells) into D, Dalt as
-    // scratch; 4 launches
+    // scratch; nlsw_kernels_per_step launches
     static cudaError_t nlsw_stages(const sl_grid *g, const void *const *fields, void *const *nodes, void *D, void *Dalt,
                                    double dt, cudaStream_t s);
     static cudaError_t flags(const sl_grid *g, const void *const *in, uint8_t *flags, cudaStream_t s);
@@ -94,6 +94,9 @@ size_t tiled2d_smem_bytes_cfgc(int nfields);
 cudaError_t launch_tiled2d_cfgd(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                                 const void *const *in, void *const *out, cudaStream_t s);
 size_t tiled2d_smem_bytes_cfgd(int nfields);
+// shallow water (sl_nlsw.cu): the viscosity nu of a grid and the launches of one step's stages
+double nlsw_viscosity(const sl_grid *g);
+int nlsw_kernels_per_step(const sl_grid *g);
 // 2-D FP32 tiled kernels of the quintic Z-spline (max_order 2; sl_tiled_z2.cu)
 cudaError_t launch_tiled2d_z2(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                               const void *const *in, void *const *out, cudaStream_t s);

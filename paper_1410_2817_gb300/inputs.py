@@ -146,11 +146,13 @@ def kelvin_fields(n: int, t: float = 0.0, amp: float = 1e-4, f0: float = 250.0) 
 
 
 def workload_kelvin(n: int = 1024, amp: float = 1e-4, f0: float = 250.0, cfl: float = 0.5,
-                    max_order: int = 2) -> Workload:
-    """The paper's Kelvin-wave test: f0 = 250, amplitude 1e-4, limiter off, to t = 1 (once round
-    the periodic box) with dt = cfl dx (unit wave speed)."""
+                    max_order: int = 2, nu: float = 0.0) -> Workload:
+    """The paper's Kelvin-wave tests: f0 = 250, amplitude 1e-4 (linear; nu = 0), or amplitude 0.5
+    with nu = 0.0005 (the nonlinear Kelvin-Poincare run), limiter off, to t = 1 (once round the
+    periodic box) with dt = cfl dx (unit wave speed)."""
     steps = int(round(1.0 / (cfl / n)))
-    return Workload(f"kelvin_{n}", 2, (n, n), 3, "nlsw", [f0], 1.0 / steps, steps, lo=(0.0, -0.5, 0.0),
+    params = [f0] if nu == 0.0 else [f0, nu]
+    return Workload(f"kelvin_{n}", 2, (n, n), 3, "nlsw", params, 1.0 / steps, steps, lo=(0.0, -0.5, 0.0),
                     hi=(1.0, 0.5, 1.0), max_order=max_order, threshold=-1.0,
                     fields=kelvin_fields(n, 0.0, amp, f0))
 

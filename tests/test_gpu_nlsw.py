@@ -49,15 +49,19 @@ def _case(name):
     return n, (0.0, -0.5), (1.0, 0.5), 20.0, 1, np.stack([h, np.zeros_like(h), np.zeros_like(h), tr, h + x1]), 0.5 / 48
 
 
-@pytest.mark.parametrize("name", ["kelvin_z2", "kelvin_z1", "simple_wave", "bump_tracers"])
-def test_step_parity_f64(sl, orc, name):
+@pytest.mark.parametrize("name,nu", [("kelvin_z2", 0.0), ("kelvin_z1", 0.0), ("simple_wave", 0.0),
+                                     ("bump_tracers", 0.0), ("bump_tracers", 0.01), ("kelvin_z2", 0.002),
+                                     ("simple_wave", 0.01)])
+def test_step_parity_f64(sl, orc, name, nu):
     n, lo, hi, f0, mo, h, dt = _case(name)
     nf = h.shape[0]
     thr = 0.25 if name == "bump_tracers" else -1.0
-    og = orc.OracleGrid(dim=2, n=n, nfields=nf, lo=lo, hi=hi, velocity="nlsw", velocity_params=[f0], max_order=mo,
+    params = [f0] if nu == 0.0 else [f0, nu]
+    og = orc.OracleGrid(dim=2, n=n, nfields=nf, lo=lo, hi=hi, velocity="nlsw", velocity_params=params, max_order=mo,
                         threshold=thr, start=orc.START_BACKWARD)
-    g = sl.Grid(2, n, nf, sl.SL_F64, lo=lo, hi=hi, velocity="nlsw", velocity_params=[f0], max_order=mo,
+    g = sl.Grid(2, n, nf, sl.SL_F64, lo=lo, hi=hi, velocity="nlsw", velocity_params=params, max_order=mo,
                 limiter_threshold=thr)
+    stage_launches = 4 if nu == 0.0 else 7  # three RK3 stages in four launches, and a stress pass each
     F = np.asarray(h, dtype=np.float64)
     for k in range(4):
         ref, nfail = orc.step(og, F, 0.0, dt, 1)
@@ -66,7 +70,7 @@ def test_step_parity_f64(sl, orc, name):
         l0 = g.diagnostics()["kernel_launches"]
         g.step(f, torch.empty_like(f), 0.0, dt, 1)
         torch.cuda.synchronize()
-        assert g.diagnostics()["kernel_launches"] - l0 == 4 + 2  # three RK3 stages in four launches, flags + remap
+        assert g.diagnostics()["kernel_launches"] - l0 == stage_launches + 2  # and flags + remap
         got = f.cpu().numpy()
         for q in range(nf):
             scale = max(float(np.abs(ref[q]).max()), 1e-300)
@@ -77,22 +81,45 @@ def test_step_parity_f64(sl, orc, name):
     assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
 
 
-def test_kelvin_f32_tiled_matches_plain(sl):
+@pytest.mark.parametrize("amp,nu", [(1e-4, 0.0), (0.5, 0.0005)])
+def test_kelvin_f32_tiled_matches_plain(sl, amp, nu):
+    """The linear Kelvin wave, and the paper's nonlinear run (amplitude 0.5, nu = 0.0005)."""
     n = 128
-    h = inputs.kelvin_fields(n)
+    h = inputs.kelvin_fields(n, 0.0, amp)
+    params = [250.0] if nu == 0.0 else [250.0, nu]
     out = {}
     for name, kern in (("tiled", sl.SL_KERNEL_AUTO), ("plain", sl.SL_KERNEL_GENERIC)):
-        g = sl.Grid(2, (n, n), 3, sl.SL_F32, lo=(0.0, -0.5), hi=(1.0, 0.5), velocity="nlsw", velocity_params=[250.0],
+        g = sl.Grid(2, (n, n), 3, sl.SL_F32, lo=(0.0, -0.5), hi=(1.0, 0.5), velocity="nlsw", velocity_params=params,
                     max_order=2, limiter_threshold=-1.0, kernel=kern)
         f = torch.tensor(h, dtype=torch.float32, device=DEV)
         l0 = g.diagnostics()["kernel_launches"]
         g.step(f, torch.empty_like(f), 0.0, 0.5 / n, 8)
         torch.cuda.synchronize()
         if name == "tiled":
-            assert g.diagnostics()["kernel_launches"] - l0 == 8 * (4 + 1)
+            assert g.diagnostics()["kernel_launches"] - l0 == 8 * ((4 if nu == 0.0 else 7) + 1)
+        d = g.diagnostics()
+        assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
         out[name] = f.double().cpu().numpy()
-    amp = float(np.abs(h[0]).max())
     assert float(np.abs(out["tiled"] - out["plain"]).max()) <= 1e-5 * amp
+
+
+def test_viscous_shear_decay_f32(sl):
+    """A shear wave u1 = 0.05 sin(2 pi x2) with nu = 0.01 decays as exp(-nu (2 pi)^2 t) on the FP32
+    production path (Z2, 64^2, to t = 0.5) within 4e-5 of its amplitude (FP32 rounding over 64
+    steps; the decay itself is 0.18 of the amplitude)."""
+    n, nu, amp, T = 64, 0.01, 0.05, 0.5
+    x = np.arange(n) / n
+    X1, X2 = np.meshgrid(x, x)
+    u = amp * np.sin(2 * np.pi * X2)
+    g = sl.Grid(2, (n, n), 3, sl.SL_F32, velocity="nlsw", velocity_params=[0.0, nu], max_order=2,
+                limiter_threshold=-1.0)
+    f = torch.tensor(np.stack([np.zeros_like(u), u, np.zeros_like(u)]), dtype=torch.float32, device=DEV)
+    steps = int(round(T / (0.5 / n)))
+    g.step(f, torch.empty_like(f), 0.0, T / steps, steps)
+    torch.cuda.synchronize()
+    got = f.double().cpu().numpy()
+    err = float(np.abs(got[1] - np.exp(-nu * (2 * np.pi) ** 2 * T) * u).max())
+    assert err <= 4e-5 * amp, err
 
 
 def test_kelvin_f32_accuracy(sl, orc):
