@@ -79,17 +79,19 @@ enum {                                                 /* velocity u(x, t) of eq
                                fields: sl_step reads them at the start of each step, and
                                sl_advect_nodes_carried replaces sl_advect_nodes.  Not fused into
                                the tiled remap and not batched.                                 */
-    SL_VEL_NLSW = 7         /* params (f0): the non-dimensional shallow-water system of Sec. 3.3,
-                               eq. (nlsw) with nu = 0, on a 2-D grid whose fields 0, 1, 2 are h, u1,
-                               u2 (further fields are passive):
-                                 Dh/Dt = -(1 + h) div u,  Du/Dt = -grad h - f (-u2, u1),
+    SL_VEL_NLSW = 7         /* params (f0) or (f0, nu >= 0): the non-dimensional shallow-water system
+                               of Sec. 3.3, eq. (nlsw), on a 2-D grid whose fields 0, 1, 2 are h,
+                               u1, u2 (further fields are passive):
+                                 Dh/Dt = -(1 + h) div u,
+                                 Du/Dt = -grad h - f (-u2, u1) + nu div[(1 + h)(grad u + grad u^T)],
                                  f = f0 x2 (x2 the node's current position).
                                Each sl_step step runs the three stages of the low-storage RK3
                                (integrator must be SL_WRK3) on the nodes -- sources by differences
                                on the node lattice (second order for max_order <= 1, fourth order
                                for 2: the Z-spline derivative at the nodes), turned physical
-                               through the Jacobian of the node positions -- then remaps once.
-                               sl_advect_nodes does not apply; not batched.                     */
+                               through the Jacobian of the node positions; with nu > 0 a stress
+                               pass precedes each stage -- then remaps once.  The workspace holds
+                               13 extra planes.  sl_advect_nodes does not apply; not batched.   */
 };
 enum { SL_NEWTON_F64 = 0, SL_NEWTON_MIXED = 1 };       /* precision of the element-map inversion  */
 enum { SL_FAIL_KEEP = 0, SL_FAIL_ERROR = 1 };          /* what a failed target reports             */
