@@ -104,7 +104,7 @@ def test_folded_cell_reports_fold(oracle_mod):
 
 def _brute_force_cells(oracle_mod, g, D, j, R):
     """All elements (unwrapped lower corners c within R of j) whose bilinear/trilinear image
-    contains target j, judged with an independent inverse."""
+    contains target j, checked with an independent inverse."""
     d = g.dim
     n = np.array(g.n[:d])
     found = []
