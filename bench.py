@@ -243,11 +243,14 @@ def kernel_only(args):
     return 0
 
 
-def batched_leg(torch, sl, inputs, steps=50, tile_config=0):
+def batched_leg(torch, sl, inputs, steps=50, tile_config=0, max_order=1):
     """512 independent 2-D grids (sides log-uniform in [32, 512], random Fourier streamfunctions,
     Gaussian + step fields, FP32), all advanced 50 steps by one persistent launch per step under a
-    CUDA graph.  The working set (~0.8 GB) is larger than L2."""
+    CUDA graph (cubic, or the quintic with max_order 2).  The working set (~0.8 GB) is larger than
+    L2."""
     wls = inputs.batched_grids(count=512, seed=0, steps=steps)
+    for wl in wls:
+        wl.max_order = max_order
     nodes = sum(wl.nnodes for wl in wls)
     grids = [sl.grid_for(wl, sl.SL_F32, tile_config=tile_config) for wl in wls]
     fields = [torch.tensor(wl.fields, dtype=torch.float32, device="cuda") for wl in wls]
@@ -266,7 +269,7 @@ def batched_leg(torch, sl, inputs, steps=50, tile_config=0):
     ms = e0.elapsed_time(e1)
     fails = sum(g.diagnostics()["fail_locate"] + g.diagnostics()["fail_fold"] + g.diagnostics()["fail_newton"]
                 for g in grids)
-    out = {"workload": "512 grids, sides 32-512 (seed 0), 2 fields, 50 steps, one graph replay",
+    out = {"workload": f"512 grids, sides 32-512 (seed 0), 2 fields, 50 steps, one graph replay, max_order {max_order}",
            "nodes": nodes, "value": nodes * steps / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
            "launches_per_call": b.info()["launches"] - l0, "tile_config": tile_config, "failed_targets": fails}
     b.close()
@@ -631,6 +634,7 @@ def main():
         gb.close()
 
     batched = batched_leg(torch, sl, inputs) if not args.no_extra else None
+    batched_z2 = batched_leg(torch, sl, inputs, max_order=2) if not args.no_extra else None
     deform3d = deform3d_leg(torch, sl, inputs) if not args.no_extra else None
     integrators = integrators_leg(torch, sl, inputs, flush) if not args.no_extra else None
     burgers = burgers_leg(torch, sl, inputs, flush) if not args.no_extra else None
@@ -680,6 +684,7 @@ def main():
         "cpu_baseline": cpu,
         "multistep_200": multistep,
         "batched": batched,
+        "batched_quintic": batched_z2,
         "deform3d_256": deform3d,
         "integrators": integrators,
         "burgers2d": burgers,

@@ -14,7 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "sl_tile2d.cuh"
+#include "sl_tile2d_z2.cuh"
 
 namespace {
 
@@ -105,6 +105,44 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
         LocalCounters cnt;
         cnt.clear();
         process_tile<Cfg, NF, true>(sa, sv, tx * Cfg::TX, ty * Cfg::TY, sm, sBox, cnt);
+        flush_counters(cnt, sa.counters);
+    }
+}
+
+// The same step for batches of quintic grids (32 x 32 tiles of the quintic tile body).
+template <int NF>
+__global__ void __launch_bounds__(CfgZ::NT, CfgZ::MINB)
+    batch_step_z2_kernel(const BatchGrid *__restrict__ table, const int *__restrict__ item_grid, int nitems,
+                         unsigned *counter, const double *__restrict__ tgrid, int k, int last)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sBox[4];
+    __shared__ int s_item;
+    __shared__ __align__(16) BatchGrid sg;
+    __shared__ TileArgs sa;
+    __shared__ VelArgs<float> sv;
+    const TileSmemZ2<NF> sm(smem);
+    for (int item = next_item(counter, &s_item); item < nitems; item = next_item(counter, &s_item)) {
+        const int gid = __ldg(item_grid + item);
+        load_entry(table, gid, &sg);
+        if (threadIdx.x == 0) {
+            sa = sg.base;
+            const bool even = (k & 1) == 0;
+            for (int f = 0; f < NF; ++f) {
+                sa.in[f] = even ? sg.fields[f] : sg.scratch[f];
+                sa.out[f] = even ? sg.scratch[f] : const_cast<float *>(sg.fields[f]);
+            }
+            sa.D = sg.steady ? sg.D[sg.dcur] : sg.D[(sg.dcur + k) & 1];
+            sa.D_next = (last || sg.steady) ? nullptr : sg.D[(sg.dcur + k + 1) & 1];
+            sv = sg.vel;
+            stage_factors(sg, tgrid[gid] + (double)(k + 1) * sg.dt, sv.ct);
+        }
+        __syncthreads();
+        const int t = item - sg.tile_base;
+        const int ty = t / sg.tiles_x, tx = t - ty * sg.tiles_x;
+        LocalCounters cnt;
+        cnt.clear();
+        process_tile_z2<NF, true>(sa, sv, tx * CfgZ::TX, ty * CfgZ::TY, sm, sBox, cnt);
         flush_counters(cnt, sa.counters);
     }
 }
@@ -206,6 +244,7 @@ void tile_counts(int cfg, const sl_grid *g, int *tx, int *ty)
 
 struct sl_batch {
     int count, nfields, cfg, nitems, num_sms;
+    bool quintic;  // the grids take the quintic Z-spline (max_order 2)
     int device;
     std::vector<sl_grid *> grids;
     char *ws;
@@ -226,8 +265,13 @@ struct sl_batch {
 // classical RK4 step per remap only
 static bool batch_eligible(const sl_grid *g)
 {
-    return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.max_order <= 1 && g->desc.walk_start == SL_START_BACKWARD &&
-           !g->carried && !g->nlsw;
+    return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.walk_start == SL_START_BACKWARD && !g->carried && !g->nlsw;
+}
+
+// Tiles of quintic batches are the quintic kernel's 32 x 32 whatever the tile configuration.
+static int batch_cfg(sl_grid *const *grids, int tile_config)
+{
+    return grids[0]->desc.max_order == 2 ? 1 : tile_config;
 }
 
 extern "C" size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int tile_config)
@@ -236,8 +280,9 @@ extern "C" size_t sl_batch_workspace_bytes(sl_grid *const *grids, int count, int
     long long nitems = 0;
     for (int q = 0; q < count; ++q) {
         if (!batch_eligible(grids[q])) return 0;
+        if ((grids[q]->desc.max_order == 2) != (grids[0]->desc.max_order == 2)) return 0;
         int tx, ty;
-        tile_counts(tile_config, grids[q], &tx, &ty);
+        tile_counts(batch_cfg(grids, tile_config), grids[q], &tx, &ty);
         nitems += (long long)tx * ty;
     }
     if (nitems > (1LL << 30)) return 0;
@@ -257,6 +302,8 @@ extern "C" sl_status sl_batch_create(sl_grid *const *grids, int count, void *con
     if (nf < 1 || nf > 4) return SL_ERR_UNSUPPORTED;
     for (int q = 0; q < count; ++q) {
         if (!batch_eligible(grids[q])) return SL_ERR_UNSUPPORTED;
+        // one batch runs one tile kernel: cubic / linear grids, or quintic grids
+        if ((grids[q]->desc.max_order == 2) != (grids[0]->desc.max_order == 2)) return SL_ERR_UNSUPPORTED;
         if (grids[q]->nfields != nf) return SL_ERR_UNSUPPORTED;
         if (!fields[q] || !scratch[q] || !isfinite(t0[q]) || !isfinite(dt[q])) return SL_ERR_ARG;
         for (int f = 0; f < nf; ++f)
@@ -269,7 +316,8 @@ extern "C" sl_status sl_batch_create(sl_grid *const *grids, int count, void *con
     if (!b) return SL_ERR_ARG;
     b->count = count;
     b->nfields = nf;
-    b->cfg = tile_config;
+    b->quintic = grids[0]->desc.max_order == 2;
+    b->cfg = batch_cfg(grids, tile_config);
     b->grids.assign(grids, grids + count);
     std::vector<BatchGrid> table(count);
     std::vector<int> items;
@@ -290,7 +338,7 @@ extern "C" sl_status sl_batch_create(sl_grid *const *grids, int count, void *con
         e.dcur = g->dcur;
         e.steady = g->steady;
         int tx, ty;
-        tile_counts(tile_config, g, &tx, &ty);
+        tile_counts(b->cfg, g, &tx, &ty);
         e.tiles_x = tx;
         e.tile_base = (int)items.size();
         for (int t = 0; t < tx * ty; ++t) items.push_back(q);
@@ -342,6 +390,33 @@ static cudaError_t launch_batch_seq(sl_batch *b, int nsteps, cudaStream_t s)
     return cudaGetLastError();
 }
 
+static_assert(CfgZ::TX == CfgA::TX && CfgZ::TY == CfgA::TY, "quintic batches reuse the 32 x 32 tile geometry");
+
+template <int NF>
+static cudaError_t launch_batch_seq_z2(sl_batch *b, int nsteps, cudaStream_t s)
+{
+    const size_t smem = z2_smem_bytes(NF);
+    static bool configured[64] = {};
+    cudaError_t e = allow_smem(batch_step_z2_kernel<NF>, b->device, smem, configured);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_z2_kernel<NF>, CfgZ::NT, smem);
+    if (e != cudaSuccess) return e;
+    const int ctas = b->num_sms * (per_sm > 0 ? per_sm : 1);
+    const int simple = b->num_sms * 8;
+    e = cudaMemsetAsync(b->counters, 0, sizeof(unsigned) * (SL_BATCH_MAX_STEPS + 2), s);
+    if (e != cudaSuccess) return e;
+    // the quintic tiles have the 32 x 32 geometry of CfgA, whose trajectory and finishing kernels serve
+    batch_advect_kernel<CfgA><<<simple, CfgA::NT, 0, s>>>(b->table, b->items, b->nitems, b->counters + 0, b->tgrid);
+    for (int k = 0; k < nsteps; ++k)
+        batch_step_z2_kernel<NF><<<ctas, CfgZ::NT, smem, s>>>(b->table, b->items, b->nitems, b->counters + 1 + k,
+                                                              b->tgrid, k, k + 1 == nsteps);
+    batch_finish_kernel<CfgA><<<simple, CfgA::NT, 0, s>>>(b->table, b->items, b->nitems,
+                                                          b->counters + 1 + SL_BATCH_MAX_STEPS, b->tgrid, b->count,
+                                                          nsteps);
+    return cudaGetLastError();
+}
+
 template <class Cfg>
 static cudaError_t launch_batch_cfg(sl_batch *b, int nsteps, cudaStream_t s)
 {
@@ -355,6 +430,14 @@ static cudaError_t launch_batch_cfg(sl_batch *b, int nsteps, cudaStream_t s)
 
 static cudaError_t launch_batch(sl_batch *b, int nsteps, cudaStream_t s)
 {
+    if (b->quintic) {
+        switch (b->nfields) {
+        case 1: return launch_batch_seq_z2<1>(b, nsteps, s);
+        case 2: return launch_batch_seq_z2<2>(b, nsteps, s);
+        case 3: return launch_batch_seq_z2<3>(b, nsteps, s);
+        default: return launch_batch_seq_z2<4>(b, nsteps, s);
+        }
+    }
     if (b->cfg == 2) return launch_batch_cfg<CfgB>(b, nsteps, s);
     if (b->cfg == 4) return launch_batch_cfg<CfgD>(b, nsteps, s);
     if (b->cfg == 3) return launch_batch_cfg<CfgC>(b, nsteps, s);

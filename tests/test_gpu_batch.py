@@ -86,6 +86,39 @@ def test_batch_matches_grids_alone(sl, tile_config, nsteps):
     assert math.isclose(info["t_first"], nsteps * wls[0].dt)
 
 
+@pytest.mark.parametrize("tile_config", [1, 3])
+def test_quintic_batch_matches_grids_alone(sl, tile_config):
+    """Grids with the quintic Z-spline run in one batch on the quintic tile body (32 x 32 tiles
+    whatever the tile configuration) and give what each grid gives alone."""
+    wls = _small_batch(7, seed=13)
+    for wl in wls:
+        wl.max_order = 2
+    grids, fields, scratch = _make(sl, wls, tile_config)
+    b = sl.Batch(grids, fields, scratch, [0.0] * len(wls), [wl.dt for wl in wls], tile_config=tile_config)
+    b.step(3)
+    torch.cuda.synchronize()
+    for q, wl in enumerate(wls):
+        dref = {}
+        ref = _alone(sl, wl, 3, 0.0, tile_config, dref)
+        got = fields[q].cpu().numpy()
+        assert _close(got, ref, max(1.0, float(np.abs(ref).max()))), (q, wl.n, float(np.abs(got - ref).max()))
+        d = grids[q].diagnostics()
+        assert d["order_hist"][2] > 0
+        assert abs(_fails(d) - _fails(dref)) <= max(2, 0.01 * _fails(dref))
+    assert b.info()["launches"] == 3 + 2
+
+
+def test_batch_rejects_mixed_orders(sl):
+    a = sl.Grid(2, (40, 40), 2, sl.SL_F32, max_order=1)
+    c = sl.Grid(2, (40, 40), 2, sl.SL_F32, max_order=2)
+    assert sl.sl_batch_workspace_bytes([a, c]) == 0
+    f = [torch.zeros((2, 40, 40), device=DEV) for _ in range(2)]
+    s = [torch.zeros_like(x) for x in f]
+    with pytest.raises(sl.SLError) as ei:
+        sl.Batch([a, c], f, s, [0.0, 0.0], [0.01, 0.01])
+    assert ei.value.status == sl.SL_ERR_UNSUPPORTED
+
+
 def test_graph_replay_equals_direct_launches(sl):
     wls = _small_batch(7, seed=5)
     res = {}
