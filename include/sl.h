@@ -217,9 +217,10 @@ sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], co
 
 /* ---- Batches: many independent 2-D FP32 grids advanced together ---------------------------
  * A batch advances count grids (created with sl_create_grid, 2-D, SL_F32, the same nfields <= 4,
- * max_order <= 1, backward walk start) by the same number of steps with one persistent launch per
- * step over a work-list of (grid, tile) items: each item is the single-grid tiled step of that
- * tile (Sec. 2.1-2.3, eq. multiZ, eq. vel).  Grids keep their own workspaces (displacements and
+ * backward walk start, an analytic velocity with any integrator and sub-step count; either all of
+ * max_order <= 1 or all quintic, max_order 2, whose tiles are 32 x 32 whatever tile_config) by the
+ * same number of steps with one persistent launch per step over a work-list of (grid, tile)
+ * items: each item is the single-grid tiled step of that tile (Sec. 2.1-2.3, eq. multiZ, eq. vel).  Grids keep their own workspaces (displacements and
  * counters).  The batch's device state (grid table, work-list, per-step work counters, grid
  * times) lives in a caller-owned workspace of sl_batch_workspace_bytes() bytes (256-byte
  * aligned); the library allocates no device memory. */
