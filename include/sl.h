@@ -77,8 +77,10 @@ enum {                                                 /* velocity u(x, t) of eq
                                Du/Dt = 0, so each node moves on the straight line X + t u(X) and
                                every integrator gives D = dt u / dx).  The trajectories need the
                                fields: sl_step reads them at the start of each step, and
-                               sl_advect_nodes_carried replaces sl_advect_nodes.  Not fused into
-                               the tiled remap and not batched.                                 */
+                               sl_advect_nodes_carried replaces sl_advect_nodes.  On the 2-D
+                               tiled path (not the pipelined configuration 5) each remap launch
+                               also writes the next step's D from its remapped velocity; not
+                               batched.                                                         */
     SL_VEL_NLSW = 7         /* params (f0) or (f0, nu >= 0): the non-dimensional shallow-water system
                                of Sec. 3.3, eq. (nlsw), on a 2-D grid whose fields 0, 1, 2 are h,
                                u1, u2 (further fields are passive):

@@ -345,9 +345,35 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
         }
         return cudaSuccess;
     }
-    // a carried velocity is read from the fields at the start of each step, so the next step's
-    // trajectories are not known inside this step's remap: carried steps are not fused
     const bool carried = g->carried != 0;
+    if (carried && use_tiled<T>(g) && (g->desc.max_order == 2 || g->desc.tile_config != 5)) {
+        // a carried velocity (Sec. 3.2) is the fields' own: the first step's D comes from the
+        // fields, each later one from the remapped velocity of the step before, written by the
+        // remap launch itself (the 2-D tiled kernels except the pipelined configuration).  The
+        // caller may change the fields between calls, so nothing is carried over to the next call.
+        g->d_cached = 0;
+        g->next_valid = 0;
+        e = counted(g, Launch<T>::advect_carried(g, cur, g->D[g->dcur], dt, s), 1);
+        if (e != cudaSuccess) return e;
+        for (int k = 0; k < nsteps; ++k) {
+            const double t = t0 + (double)k * dt;
+            const int nx = g->dcur ^ 1;
+            void *dnext = k + 1 < nsteps ? g->D[nx] : nullptr;
+            e = counted(g, Launch<T>::step_fused(g, g->D[g->dcur], dnext, t + dt, dt, cur, nxt, s),
+                        tiled_kernels_per_call(g));
+            if (e != cudaSuccess) return e;
+            if (dnext) g->dcur = nx;
+            for (int q = 0; q < g->nfields; ++q) {
+                void *tmp = nxt[q];
+                nxt[q] = (void *)cur[q];
+                cur[q] = tmp;
+            }
+        }
+        if (nsteps % 2 == 1) e = counted(g, Launch<T>::copy_planes(g, cur, fields, s), 1);
+        return e;
+    }
+    // otherwise a carried velocity is read from the fields at the start of each step by its own
+    // launch before the remap
     const bool fused = use_tiled<T>(g) && !carried;
     // steady velocity: one integration serves every step (and later calls with the same dt)
     const bool reuse = g->steady != 0;

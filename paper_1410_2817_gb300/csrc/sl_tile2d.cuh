@@ -56,6 +56,9 @@ struct TileArgs {
     const float *in[SL_MAX_FIELDS];
     float *out[SL_MAX_FIELDS];
     DevCounters *counters;
+    // carried velocity (Sec. 3.2): D_next = dt u / dx from the remapped fields vf[0], vf[1]
+    int carried, vf[2];
+    float csc[2];
 };
 
 __device__ __forceinline__ long long gidx(int x, int y, int n0, int n1)
@@ -663,6 +666,22 @@ __device__ __forceinline__ void integrate_next(const TileArgs &a, const VelArgs<
     }
 }
 
+// Sec. 3.2: the next step's displacements of a carried velocity are the remapped velocity of the
+// tile's own targets, D = dt u / dx; each thread reads back the outputs it wrote itself.
+template <class Cfg>
+__device__ __forceinline__ void carried_next(const TileArgs &a, int x0, int y0)
+{
+    const int tx = threadIdx.x % Cfg::TX, ty = threadIdx.x / Cfg::TX;
+#pragma unroll 1
+    for (int k = 0; k < Cfg::TPT; ++k) {
+        const int jx = x0 + tx, jy = y0 + ty + k * Cfg::ROWS;
+        if (jx >= a.n0 || jy >= a.n1) continue;
+        const long long jj = (long long)jy * a.n0 + jx;
+        reinterpret_cast<float2 *>(a.D_next)[jj] =
+            make_float2(a.csc[0] * a.out[a.vf[0]][jj], a.csc[1] * a.out[a.vf[1]][jj]);
+    }
+}
+
 // One TX x TY tile of targets with origin (x0, y0), staged and computed in one pass: every thread
 // of the CTA calls this; it synchronises the CTA.
 template <class Cfg, int NF, bool FUSED>
@@ -697,10 +716,11 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     // ---- phase 2: stage displacements and fields of the window (all copies in flight) -------
     stage_window<Cfg, NF>(a, w, sm.D, sm.H);
     clear_flags<Cfg, NF>(a, w, sm.M);
-    if (FUSED && a.D_next != nullptr) integrate_next<Cfg>(a, vn, x0, y0);
+    if (FUSED && a.D_next != nullptr && !a.carried) integrate_next<Cfg>(a, vn, x0, y0);
     cp_async_wait_all();
     __syncthreads();
     tile_compute<Cfg, NF>(a, x0, y0, w, staged, sm.D, sm.H, sm.S, sm.M, sm.B, cnt);
+    if (FUSED && a.D_next != nullptr && a.carried) carried_next<Cfg>(a, x0, y0);
 }
 
 template <class Cfg, int NF, bool FUSED>
@@ -847,6 +867,17 @@ __host__ inline TileArgs make_tile_args(const sl_grid *g, const void *D, void *D
     return a;
 }
 
+// fused steps of a carried velocity take the next step's D from the remapped velocity fields
+__host__ inline void set_carried(const sl_grid *g, double dt, TileArgs &a)
+{
+    if (!g->carried) return;
+    a.carried = 1;
+    for (int c = 0; c < 2; ++c) {
+        a.vf[c] = g->vel_field[c];
+        a.csc[c] = (float)(dt / g->dx[c]);
+    }
+}
+
 // opt-in shared memory above 48 KB is a per-device function attribute: set it once per device
 template <class K>
 __host__ cudaError_t allow_smem(K kernel, int device, size_t bytes, bool *configured)
@@ -931,8 +962,9 @@ template <class Cfg>
 __host__ cudaError_t launch_tiled_cfg(const sl_grid *g, const void *D, void *D_next, double t_next, double dt,
                                       bool fused, const void *const *in, void *const *out, cudaStream_t s)
 {
-    const TileArgs a = make_tile_args(g, D, D_next, in, out);
+    TileArgs a = make_tile_args(g, D, D_next, in, out);
     if (fused) {
+        set_carried(g, dt, a);
         const VelArgs<float> vn = make_vel_args<float>(g, t_next, dt);
         return launch_tiled_fused<Cfg, true>(g, a, vn, s);
     }

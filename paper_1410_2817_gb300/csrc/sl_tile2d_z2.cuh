@@ -428,10 +428,11 @@ __device__ __forceinline__ void process_tile_z2(const TileArgs &a, const VelArgs
         const int nm = NF * w.wy * ((w.wx + 31) >> 5);
         for (int q = threadIdx.x; q < nm; q += NT) sm.M[q] = 0u;
     }
-    if (FUSED && a.D_next != nullptr) integrate_next<CfgZ>(a, vn, x0, y0);
+    if (FUSED && a.D_next != nullptr && !a.carried) integrate_next<CfgZ>(a, vn, x0, y0);
     cp_async_wait_all();
     __syncthreads();
     tile_compute_z2<NF>(a, x0, y0, w, staged, sm, cnt);
+    if (FUSED && a.D_next != nullptr && a.carried) carried_next<CfgZ>(a, x0, y0);
 }
 
 }  // namespace

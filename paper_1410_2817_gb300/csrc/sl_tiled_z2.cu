@@ -49,10 +49,11 @@ cudaError_t launch_z2(const sl_grid *g, const TileArgs &a, const VelArgs<float> 
 cudaError_t launch_tiled2d_z2(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                               const void *const *in, void *const *out, cudaStream_t s)
 {
-    const TileArgs a = make_tile_args(g, D, D_next, in, out);
+    TileArgs a = make_tile_args(g, D, D_next, in, out);
     VelArgs<float> vn;
     memset(&vn, 0, sizeof(vn));
     if (fused) {
+        set_carried(g, dt, a);
         vn = make_vel_args<float>(g, t_next, dt);
         return launch_z2<true>(g, a, vn, s);
     }
