@@ -42,7 +42,7 @@ FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at 1024^2 (3 fields) of the fused step
 # kernel (the headline's only launch) and of the plain remap kernel (sl_remap_fields), from the ncu
 # captures summarised in profiles/; valid only for the kernel source they were taken on.
-NCU_TRAFFIC = {"step_bytes_per_launch": 21071232, "remap_bytes_per_launch": 21037056, "source_sha": "4153495458d1c16e"}
+NCU_TRAFFIC = {"step_bytes_per_launch": 21063680, "remap_bytes_per_launch": 21037312, "source_sha": "4e7dd28e29c7f207"}
 
 
 def _source_sha() -> str:
