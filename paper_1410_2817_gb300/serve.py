@@ -187,9 +187,12 @@ class GpuExecutor:
         return w
 
     def _lane_key(self, st: JobState):
+        """2-D FP32 jobs with a given velocity and at most 4 fields share a batch lane per field
+        count and spline family (cubic / linear, or quintic); the others run in their own lane."""
         wl = st.job.workload
-        if self.dtype_code(self.sl, st.job) == self.sl.SL_F32 and wl.dim == 2 and wl.nfields <= 4:
-            return ("batch", wl.nfields)
+        if (self.dtype_code(self.sl, st.job) == self.sl.SL_F32 and wl.dim == 2 and wl.nfields <= 4
+                and wl.velocity not in ("carried", "nlsw")):
+            return ("batch", wl.nfields, wl.max_order == 2)
         return ("job", st.job.job_id)
 
     def start(self, st: JobState, fields):

@@ -86,3 +86,32 @@ def test_served_job_accuracy(serve):
         got = out["results"][j.job_id].astype(np.float64)
         l1 = np.abs(got[0] - ref[0]).sum() / np.abs(ref[0]).sum()
         assert l1 <= 1e-4, l1
+
+
+def test_other_job_kinds_in_the_mix(serve):
+    """Quintic, Burgers (carried velocity) and shallow-water jobs served beside ordinary ones: the
+    quintic jobs share a batch lane of their own, the Burgers and shallow-water jobs run in their
+    own lanes, and every result equals the job run alone."""
+    base = _trace()[:6]
+    z2 = inputs.workload_swirl(64, steps=4)
+    z2.max_order = 2
+    extra = [z2, inputs.workload_burgers(64, steps=5), inputs.workload_kelvin(64)]
+    extra[2].steps = 4
+    jobs = list(base)
+    for q, wl in enumerate(extra):
+        jobs.append(inputs.Job(100 + q, 0.01 * q, wl, "f32"))
+
+    def fields_of(job):
+        wl = job.workload
+        if job.job_id >= 100:
+            return torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+        return _fields_of(job)
+
+    mix = serve.serve_trace(jobs, fields_of, budget_bytes=8 << 30, keep_results=True)
+    assert mix["completed"] == len(jobs) and mix["rejected"] == 0
+    for job in jobs:
+        alone = serve.serve_trace([inputs.Job(job.job_id, 0.0, job.workload, job.dtype)], fields_of,
+                                  budget_bytes=8 << 30, keep_results=True)
+        a, b = mix["results"][job.job_id], alone["results"][job.job_id]
+        scale = max(1e-3, float(np.abs(b).max()))
+        assert float(np.abs(a - b).max()) <= 1e-6 * scale, (job.job_id, job.workload.name)
