@@ -178,6 +178,34 @@ def cpu_baseline(budget_s: float = 10.0, steps_max: int = 400):
                                         "note": "moments m_0..m_2 relative to the field's L1 mass"}}
 
 
+def cpu_oracle_rows(steps: int = 2):
+    """The oracle, as it stands, on the other workloads the bench measures (each a bounded sample
+    of `steps` whole 1024^2 steps on the host cores), for the rows beside the headline: Williamson's
+    RK3, the quintic Z-spline, 2-D Burgers and the shallow-water Kelvin wave (linear and
+    nonlinear viscous)."""
+    from oracle import oracle
+    from paper_1410_2817_gb300 import inputs
+    out = {}
+    wl_sw = inputs.workload_swirl(N_SIDE)
+    wl_z2 = inputs.workload_swirl(N_SIDE)
+    wl_z2.max_order = 2
+    rows = (("integrators_wrk3", wl_sw, {"integrator": "wrk3"}),
+            ("quintic_z2", wl_z2, {}),
+            ("burgers2d", inputs.workload_burgers(N_SIDE), {}),
+            ("nlsw_kelvin_linear", inputs.workload_kelvin(N_SIDE), {}),
+            ("nlsw_kelvin_nonlinear_viscous", inputs.workload_kelvin(N_SIDE, amp=0.5, nu=0.0005), {}))
+    for name, wl, kw in rows:
+        og = oracle.OracleGrid(dim=wl.dim, n=wl.n, nfields=wl.nfields, lo=wl.lo, hi=wl.hi, velocity=wl.velocity,
+                               velocity_params=list(wl.velocity_params), max_order=wl.max_order,
+                               threshold=wl.threshold, **kw)
+        t0 = time.perf_counter()
+        oracle.step(og, wl.fields, wl.t0, wl.dt, steps)
+        el = time.perf_counter() - t0
+        out[name] = {"value": wl.nnodes * steps / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                     "sample": f"{steps} full step(s) of {wl.name}, FP64"}
+    return out
+
+
 def run_reference(args):
     dist, rank, ws, local = (None, 0, 1, 0)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
@@ -278,27 +306,35 @@ def batched_leg(torch, sl, inputs, steps=50, tile_config=0, max_order=1):
 
 def deform3d_leg(torch, sl, inputs, steps=5):
     """3-D 256^3 deformation flow (T = 3, dt = 0.03), two fields, FP32 bulk with FP64 re-solves of
-    degenerate elements: `steps` full steps through sl_step, L2 flushed before each."""
-    wl = inputs.workload_deform3d(256, steps=steps)
-    g = sl.grid_for(wl, sl.SL_F32)
-    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
-    s = torch.empty_like(f)
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    g.step(f, s, 0.0, wl.dt, 1)
-    ms = []
-    t = wl.dt
-    for k in range(steps):
-        flush.fill_(k)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.step(f, s, t, wl.dt, 1)
-        b.record()
-        ms.append((a, b))
-        t += wl.dt
-    torch.cuda.synchronize()
-    tot = sum(a.elapsed_time(b) for a, b in ms)
-    return {"workload": "deform3d 256^3, 2 fields, FP32", "value": wl.nnodes * steps / (tot * 1e-3), "unit": UNIT,
-            "ms_per_step": tot / steps}
+    degenerate elements: `steps` full steps through sl_step, L2 flushed before each; and the same
+    with the quintic Z-spline (plain kernels: 6 x 6 x 6 taps per field)."""
+    out = {}
+    for name, mo, nsteps in (("cubic", 1, steps), ("quintic_plain", 2, 2)):
+        wl = inputs.workload_deform3d(256, steps=nsteps)
+        wl.max_order = mo
+        g = sl.grid_for(wl, sl.SL_F32)
+        f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+        s = torch.empty_like(f)
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        g.step(f, s, 0.0, wl.dt, 1)
+        ms = []
+        t = wl.dt
+        for k in range(nsteps):
+            flush.fill_(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.step(f, s, t, wl.dt, 1)
+            b.record()
+            ms.append((a, b))
+            t += wl.dt
+        torch.cuda.synchronize()
+        tot = sum(a.elapsed_time(b) for a, b in ms)
+        out[name] = {"workload": f"deform3d 256^3, 2 fields, FP32, max_order {mo}",
+                     "value": wl.nnodes * nsteps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / nsteps}
+        g.close()
+    res = dict(out["cubic"])
+    res["quintic_plain"] = out["quintic_plain"]
+    return res
 
 
 def integrators_leg(torch, sl, inputs, flush, steps=10):
@@ -678,6 +714,7 @@ def main():
             dist.destroy_process_group()
         return 0
     cpu = None if args.no_cpu_baseline else cpu_baseline()
+    cpu_rows = None if (args.no_cpu_baseline or args.no_extra) else cpu_oracle_rows()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -699,6 +736,7 @@ def main():
                            "algorithmic_bytes_per_launch": alg_bytes, "bytes_rule": "d T + 2 F T per node (32 B)",
                            "launch_ms": remap_ms, "advect_ms": advect_ms},
         "cpu_baseline": cpu,
+        "cpu_oracle_other_rows": cpu_rows,
         "multistep_200": multistep,
         "batched": batched,
         "batched_quintic": batched_z2,
