@@ -515,11 +515,17 @@ __global__ void __launch_bounds__(256) copy_planes_kernel(long long N, int nf, F
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     if (VEC) {
+        // every plane's vector at once: nf independent 16-byte loads in flight per thread; the
+        // source (the scratch planes) is not read again before it is overwritten
         const long long nv = N * (long long)sizeof(T) / 16;
-        for (int q = 0; q < nf; ++q) {
-            const float4 *src = reinterpret_cast<const float4 *>(f.in[q]);
-            float4 *dst = reinterpret_cast<float4 *>(f.out[q]);
-            for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += stride) dst[i] = src[i];
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += stride) {
+            float4 v[SL_MAX_FIELDS];
+#pragma unroll
+            for (int q = 0; q < SL_MAX_FIELDS; ++q)
+                if (q < nf) v[q] = __ldcs(reinterpret_cast<const float4 *>(f.in[q]) + i);
+#pragma unroll
+            for (int q = 0; q < SL_MAX_FIELDS; ++q)
+                if (q < nf) reinterpret_cast<float4 *>(f.out[q])[i] = v[q];
         }
     } else {
         for (int q = 0; q < nf; ++q)
