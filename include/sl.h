@@ -109,7 +109,7 @@ typedef struct {
     int nfields;                    /* 1..8 fields advected together                                 */
     int dtype;                      /* SL_F64 or SL_F32                                              */
     int max_order;                  /* m_max of the Z-spline: 0 (linear), 1 (cubic) or 2 (quintic;
-                                       plain kernels only)                                          */
+                                       tiled in 2-D FP32, plain kernels in 3-D and FP64)            */
     double limiter_threshold;       /* 0.25 in the paper (Sec. 2.3); < 0 disables the limiter        */
     int integrator;                 /* SL_RK4 or SL_WRK3                                             */
     int velocity_kind;              /* SL_VEL_*                                                      */
