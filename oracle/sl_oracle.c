@@ -26,7 +26,7 @@
  *     one flag bit per field.
  *   - The element map is expanded about the cell's lower corner; the Newton start is the solution
  *     of the linear part; the stop rule is max|dxi| <= tol (default 1e-14) or max_iter (8).
- *   - Search start "opposite to the velocity": the element that has Lagrangian node j as a vertex
+ *   - Search start against the node's velocity: the element that has Lagrangian node j as a vertex
  *     on the side opposite its own step displacement (c_a = j_a - [D_j,a > 0]).  A target within
  *     `slack` of a face is accepted in the first element the walk reaches.
  *   - Order reduction is isotropic and per field: m drops while any flag lies in [c-m, c+m+1]^d.
