@@ -4,10 +4,11 @@ Jobs arrive over time (2-D or 3-D grids of different sizes, field counts, step c
 precisions).  The server keeps every admitted job's grid and fields resident in device memory and
 advances ALL active jobs by one step per iteration:
 
-* 2-D FP32 jobs with the same field count form one batch (sl_batch_step: one persistent launch
-  over a work-list of tiles of all those grids), rebuilt only when its membership changes;
-* 3-D and FP64 jobs are stepped with sl_step, each on its own stream, so their kernels run
-  concurrently with the batches.
+* 2-D FP32 jobs with a given velocity, the same field count and the same spline family (cubic /
+  linear, or quintic) form one batch (sl_batch_step: one persistent launch over a work-list of
+  tiles of all those grids), rebuilt only when its membership changes;
+* 3-D, FP64, carried-velocity (Burgers) and shallow-water jobs are stepped with sl_step, each on
+  its own stream, so their kernels run concurrently with the batches.
 
 Each of these lanes is relaunched as soon as its previous step has finished (an event per lane,
 polled by the host loop): slow FP64 jobs never hold back the FP32 batches.  Arrived jobs are
