@@ -169,3 +169,25 @@ def test_burgers_f32_against_oracle(sl, orc):
     s_ref = np.hypot(ref[0], ref[1])[64, 64:]
     s_got = np.hypot(got[0], got[1])[64, 64:]
     assert int(np.argmax(s_ref)) == int(np.argmax(s_got))
+
+
+def test_burgers_quintic_fused_matches_plain(sl):
+    """Burgers with the quintic Z-spline: the quintic tile kernel writes the next step's D from its
+    own remapped velocity as the cubic one does (one launch per step after the first), and two
+    steps from the same fields give the plain FP32 kernels' values."""
+    wl = inputs.workload_burgers(192)
+    wl.max_order = 2
+    gt = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_AUTO)
+    gg = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_GENERIC)
+    f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
+    gg.step(f, torch.empty_like(f), 0.0, wl.dt, 30)  # let the shock form
+    t = 30 * wl.dt
+    ft, fg = f.clone(), f.clone()
+    l0 = gt.diagnostics()["kernel_launches"]
+    gt.step(ft, torch.empty_like(ft), t, wl.dt, 2)
+    assert gt.diagnostics()["kernel_launches"] - l0 == 1 + 2
+    gg.step(fg, torch.empty_like(fg), t, wl.dt, 2)
+    torch.cuda.synchronize()
+    diff = (ft - fg).abs()
+    assert float((diff > 2e-5).float().mean()) <= 1e-3 and float(diff.max()) <= 0.1, float(diff.max())
+    assert gt.diagnostics()["order_hist"][2] > 0
