@@ -527,6 +527,29 @@ def burgers_leg(torch, sl, inputs, flush, steps=10):
     return out
 
 
+def moments_leg(torch, sl, inputs, flush, calls=10):
+    """Sec. 3.1 discrete moments m_0..m_4 of one 1024^2 FP32 field plane (sl_moments: per-block
+    FP64 partial sums in a fixed order, a final block, the 5 doubles read back; the call
+    synchronises), L2 flushed before each call.  Host time per call, the read-back included."""
+    wl = inputs.workload_swirl(N_SIDE)
+    g = sl.grid_for(wl, sl.SL_F32)
+    f = torch.tensor(wl.fields[0], dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        flush.fill_(0)
+        g.moments(f, 4)
+    ts = []
+    for q in range(calls):
+        flush.fill_(q & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = g.moments(f, 4)
+        ts.append(time.perf_counter() - t0)
+    g.close()
+    ms = 1e3 * sum(ts) / calls
+    return {"workload": f"moments m_0..m_4 of one {N_SIDE}^2 FP32 plane", "ms_per_call": ms,
+            "value": wl.nnodes / (ms * 1e-3), "unit": "nodes/s", "m0": m[0]}
+
+
 def serving_leg(njobs, rank=0, world=1, budget_gb=120.0, rate_hz=200.0, policy="sjf", max_active=16):
     """The first `njobs` jobs of the served trace (Poisson arrivals, mean `rate_hz` jobs/s -- 200 for
     the configured trace --, seed 1; 70 % 2-D 64^2-2048^2, 30 % 3-D 32^3-192^3, 1-4 fields, 10-200
@@ -734,6 +757,7 @@ def main():
     burgers = burgers_leg(torch, sl, inputs, flush) if not args.no_extra else None
     quintic = quintic_leg(torch, sl, inputs, flush) if not args.no_extra else None
     nlsw = nlsw_leg(torch, sl, inputs, flush) if not args.no_extra else None
+    moments = moments_leg(torch, sl, inputs, flush) if not args.no_extra else None
     if not args.no_extra and args.serve_jobs > 0:
         # untimed warm-up of the served trace: the first use of each kernel variant (2-D / 3-D,
         # FP32 / FP64, 1-4 fields) loads it, and the caching allocator grows to the job mix; both
@@ -786,6 +810,7 @@ def main():
         "burgers2d": burgers,
         "quintic_z2": quintic,
         "nlsw_kelvin": nlsw,
+        "moments": moments,
         "serving": serving,
         "serving_sustained_rate": serving_light,
         "serving_fifo_uncapped": serving_fifo,
