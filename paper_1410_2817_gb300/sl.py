@@ -309,6 +309,7 @@ class Grid:
         return torch.empty((self.nfields,) + self.shape, dtype=self.torch_dtype, device=self.workspace.device)
 
     def advect(self, t, dt, stream=None):
+        """Trajectories of the grid's analytic velocity over [t, t + dt] into the grid's D."""
         sl_advect_nodes(self.handle, t, dt, stream)
 
     def advect_carried(self, fields, dt, stream=None):
@@ -327,17 +328,18 @@ class Grid:
         sl_remap_fields(self.handle, self._fit(fin), self._fit(fout), stream)
 
     def remap_debug(self, fin, fout, stream=None):
+        """sl_remap_fields with per-target outputs: (cell, xi, order, status) tensors."""
         dev = fin.device
-        N = self.nnodes
         cell = torch.empty(self.shape, dtype=torch.int64, device=dev)
         xi = torch.empty(self.shape + (self.dim,), dtype=torch.float64, device=dev)
         order = torch.empty((self.nfields,) + self.shape, dtype=torch.uint8, device=dev)
         status = torch.empty(self.shape, dtype=torch.uint8, device=dev)
         sl_remap_fields_debug(self.handle, list(fin), list(fout), cell, xi, order, status, stream)
-        del N
         return cell, xi, order, status
 
     def step(self, fields: torch.Tensor, scratch: torch.Tensor, t0, dt, nsteps, stream=None):
+        """nsteps full steps from t0, in place on `fields` (`scratch`: the other half of the
+        ping-pong pair, same shape)."""
         sl_step(self.handle, self._fit(fields), self._fit(scratch), t0, dt, nsteps, stream)
 
     def moments(self, field: torch.Tensor, pmax=4, stream=None):
