@@ -70,6 +70,8 @@ MUTATIONS = {
     "nlsw_stress_normal": ("tau[i] = d * 2.0 * ux;", "tau[i] = d * ux;", "test_oracle_nlsw.py"),
     "nlsw_stress_shear": ("tau[N + i] = d * (uy + vx);", "tau[N + i] = d * uy;", "test_oracle_nlsw.py"),
     "nlsw_viscous_sign": ("S[1] += nu * (t11x + t12y);", "S[1] -= nu * (t11x + t12y);", "test_oracle_nlsw.py"),
+    "nlsw_stage_weight": ("B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};", "B[3] = {1.0 / 3.0, 0.5, 8.0 / 15.0};",
+                          "test_oracle_nlsw.py"),
     "moment_centre": ("cen[a] = 0.5 * (g->lo[a] + g->hi[a]);", "cen[a] = 0.5 * (g->hi[a] - g->lo[a]);",
                       "test_oracle_step.py"),
 }
