@@ -72,6 +72,11 @@ MUTATIONS = {
     "nlsw_viscous_sign": ("S[1] += nu * (t11x + t12y);", "S[1] -= nu * (t11x + t12y);", "test_oracle_nlsw.py"),
     "nlsw_stage_weight": ("B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};", "B[3] = {1.0 / 3.0, 0.5, 8.0 / 15.0};",
                           "test_oracle_nlsw.py"),
+    "step_time": ("double t = t0 + (double)s * dt;", "double t = t0;", "test_oracle_step.py"),
+    "cramer_column": ("M[a][b] = (b == c) ? r[a] : J[a][b];", "M[a][b] = (a == c) ? r[b] : J[a][b];",
+                      "test_oracle_mapping.py"),
+    "moment_power": ("for (int q = 0; q < p; ++q) rp *= r;", "for (int q = 1; q < p; ++q) rp *= r;",
+                     "test_oracle_step.py"),
     "moment_centre": ("cen[a] = 0.5 * (g->lo[a] + g->hi[a]);", "cen[a] = 0.5 * (g->hi[a] - g->lo[a]);",
                       "test_oracle_step.py"),
 }
