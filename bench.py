@@ -237,7 +237,6 @@ def cpu_oracle_rows(steps: int = 2):
 
 
 def run_reference(args):
-    dist, rank, ws, local = (None, 0, 1, 0)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
         return 0
     from oracle import oracle
@@ -662,7 +661,7 @@ def main():
     if sampler:
         sampler.start()
         time.sleep(0.3)  # nvidia-smi's first sample
-    g32, f32, s32, ms32, wall32, t_end, launches = run_path(sl.SL_F32, sl.SL_NEWTON_MIXED, args.steps, args.warmup)
+    g32, f32, s32, ms32, _, t_end, launches = run_path(sl.SL_F32, sl.SL_NEWTON_MIXED, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
     dev_ms = sum(ms32)
     dev_ms_max = _max_over_ranks(dist, torch, dev_ms)
@@ -725,7 +724,7 @@ def main():
     gm.close()
 
     # ---- plain FP64 GPU path ----------------------------------------------------------------
-    g64, _, _, ms64, _, _, _ = run_path(sl.SL_F64, sl.SL_NEWTON_F64, args.fp64_steps, 3)
+    _, _, _, ms64, _, _, _ = run_path(sl.SL_F64, sl.SL_NEWTON_F64, args.fp64_steps, 3)
     fp64_value = ws * N * args.fp64_steps / (_max_over_ranks(dist, torch, sum(ms64)) * 1e-3)
 
     # ---- end to end through the public API with host buffers ---------------------------------

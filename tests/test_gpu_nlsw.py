@@ -109,7 +109,7 @@ def test_viscous_shear_decay_f32(sl):
     steps; the decay itself is 0.18 of the amplitude)."""
     n, nu, amp, T = 64, 0.01, 0.05, 0.5
     x = np.arange(n) / n
-    X1, X2 = np.meshgrid(x, x)
+    _, X2 = np.meshgrid(x, x)
     u = amp * np.sin(2 * np.pi * X2)
     g = sl.Grid(2, (n, n), 3, sl.SL_F32, velocity="nlsw", velocity_params=[0.0, nu], max_order=2,
                 limiter_threshold=-1.0)

@@ -213,7 +213,7 @@ def test_fused_tiled_step_matches_plain_f32(sl):
     gt = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_AUTO)
     gg = sl.grid_for(wl, sl.SL_F32, kernel=sl.SL_KERNEL_GENERIC)
     f = torch.tensor(wl.fields, dtype=torch.float32, device=DEV)
-    t, worst = 0.25, 0.0
+    t = 0.25
     for _ in range(3):
         ft, fg = f.clone(), f.clone()
         gt.step(ft, torch.empty_like(ft), t, wl.dt, 2)
