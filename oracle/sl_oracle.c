@@ -680,9 +680,6 @@ static double lattice_derivative(const or_grid *g, const double *w, const int64_
     return ((2.0 / 3.0) * d1 - (1.0 / 12.0) * d2) / dxa;
 }
 
-/* One step of the shallow-water system: h (nfields planes) is replaced by the remapped fields.
- * Scratch: W (nfields planes), q (3 planes), e and qx (2 planes each), D (2 per node),
- * flags (N), tmp (nfields planes).  Returns the failed targets of the remap. */
 /* Jacobian J = dx/dX of the node positions at node k (e: displacement planes, physical units)
  * and its inverse, row-major I[0..3] = (J^-1)_00, _01, _10, _11. */
 static void node_jacobian_inverse(const or_grid *g, const double *ex, const double *ey, const int64_t k[3],
@@ -697,6 +694,9 @@ static void node_jacobian_inverse(const or_grid *g, const double *ex, const doub
     I[3] = J00 / det;
 }
 
+/* One step of the shallow-water system: h (nfields planes) is replaced by the remapped fields.
+ * Scratch: W (nfields planes), q (3 planes), e and qx (2 planes each), D (2 per node),
+ * flags (N), tmp (nfields planes).  Returns the failed targets of the remap. */
 static int64_t or_nlsw_step(const or_grid *g, double *h, double dt, double *W, double *q, double *e, double *qx,
                             double *tau, double *D, uint8_t *flags, double *tmp)
 {

@@ -70,6 +70,10 @@ MUTATIONS = {
     "nlsw_stress_normal": ("tau[i] = d * 2.0 * ux;", "tau[i] = d * ux;", "test_oracle_nlsw.py"),
     "nlsw_stress_shear": ("tau[N + i] = d * (uy + vx);", "tau[N + i] = d * uy;", "test_oracle_nlsw.py"),
     "nlsw_viscous_sign": ("S[1] += nu * (t11x + t12y);", "S[1] -= nu * (t11x + t12y);", "test_oracle_nlsw.py"),
+    "nlsw_jacobian_transposed": ("I[1] = -J01 / det;\n    I[2] = -J10 / det;", "I[1] = -J10 / det;\n    I[2] = -J01 / det;",
+                                 "test_oracle_nlsw.py"),
+    "nlsw_jacobian_axis": ("J01 = lattice_derivative(g, ex, k, 1, dx[1]);", "J01 = lattice_derivative(g, ex, k, 0, dx[1]);",
+                           "test_oracle_nlsw.py"),
     "nlsw_stage_weight": ("B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};", "B[3] = {1.0 / 3.0, 0.5, 8.0 / 15.0};",
                           "test_oracle_nlsw.py"),
     "step_time": ("double t = t0 + (double)s * dt;", "double t = t0;", "test_oracle_step.py"),
