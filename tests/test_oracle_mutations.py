@@ -76,6 +76,8 @@ MUTATIONS = {
                            "test_oracle_nlsw.py"),
     "nlsw_difference_fd2": ("if (g->max_order < 2) return 0.5 * d1 / dxa;", "if (g->max_order < 2) return d1 / dxa;",
                             "test_oracle_nlsw.py"),
+    "nlsw_coriolis_position": ("const double y = g->lo[1] + (double)k[1] * dx[1] + ey[i];",
+                               "const double y = g->lo[1] + (double)k[1] * dx[1];", "test_oracle_nlsw.py"),
     "nlsw_stage_weight": ("B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};", "B[3] = {1.0 / 3.0, 0.5, 8.0 / 15.0};",
                           "test_oracle_nlsw.py"),
     "step_time": ("double t = t0 + (double)s * dt;", "double t = t0;", "test_oracle_step.py"),

@@ -180,3 +180,34 @@ def test_viscous_damped_gravity_wave(orc):
     w = np.sqrt(kap ** 2 - a ** 2)
     H = amp * np.exp(-a * T) * (np.cos(w * T) + a / w * np.sin(w * T))
     assert np.abs(out[0] - H * np.cos(kap * x)[None]).max() <= 2e-4 * amp
+
+
+def test_zonal_absolute_momentum_on_the_beta_plane(orc):
+    """Reading of eq. (nlsw): the Coriolis parameter f = f0 x2 is taken at the node's current
+    position.  For fields independent of x1 there is no zonal pressure force, so each node keeps
+    its absolute momentum u1 - f0 x2^2 / 2; while h stays O(dt^3) (one step from rest in h with a
+    uniform meridional stream V) a node follows x2' = u2, u1' = f0 x2 u2, u2' = -f0 x2 u1.  The
+    oracle's step against that ODE solved tightly and traced back from every target; f taken at
+    the node's starting position instead would shift u1 by f0 (V dt)^2 / 2 = 5.6e-4."""
+    solve_ivp = pytest.importorskip("scipy.integrate").solve_ivp
+    brentq = pytest.importorskip("scipy.optimize").brentq
+    f0, V, ny, dt = 5.0, 0.3, 32, 0.05
+    g = _nlsw_grid(orc, (4, ny), 1, f0=f0)
+    h = np.zeros((3, ny, 4))
+    h[2] = V
+    out, nfail = _run(orc, g, h, dt, 1)
+    assert nfail == 0
+
+    def node(y0):
+        r = solve_ivp(lambda t, s: [s[2], f0 * s[0] * s[2], -f0 * s[0] * s[1]], (0.0, dt), [y0, 0.0, V],
+                      rtol=1e-13, atol=1e-15)
+        return r.y[:, -1]
+
+    y = -0.5 + np.arange(ny) / ny
+    # away from the periodic seam, where f = f0 x2 jumps from +f0/2 to -f0/2
+    for j in np.nonzero(np.abs(y) < 0.3)[0]:
+        y0 = brentq(lambda a: node(a)[0] - y[j], y[j] - 0.1, y[j] + 0.1, xtol=1e-15)
+        _, ue, ve = node(y0)
+        assert np.abs(out[1][j] - ue).max() <= 5e-6, (y[j], out[1][j], ue)
+        assert np.abs(out[2][j] - ve).max() <= 5e-6, (y[j], out[2][j], ve)
+        assert np.abs(out[:, j] - out[:, j, :1]).max() == 0.0  # still independent of x1
