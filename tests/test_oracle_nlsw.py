@@ -1,8 +1,9 @@
-"""Oracle pins for the shallow-water system (Sec. 3.3, eq. nlsw, nu = 0) on the moving nodes:
-closed-form solutions the paper names or that the equations admit -- the equatorial Kelvin wave
-(eq. kelvin), a standing gravity wave (linear dispersion omega = kappa), a nonlinear simple wave
-(Riemann invariant u - 2 sqrt(1 + h) constant) -- each with its convergence rate, and the finite
-differences pinned to the Z-spline derivatives they are defined by."""
+"""Oracle pins for the shallow-water system (Sec. 3.3, eq. nlsw) on the moving nodes: closed-form
+solutions the paper names or that the equations admit -- the equatorial Kelvin wave (eq. kelvin),
+a standing gravity wave (linear dispersion omega = kappa), a nonlinear simple wave (Riemann
+invariant u - 2 sqrt(1 + h) constant), with viscosity a decaying shear wave and a damped gravity
+wave -- each with its convergence rate or bound; the zonal absolute momentum a node keeps on the
+beta plane; and the finite differences pinned to the Z-spline derivatives they are defined by."""
 import numpy as np
 import pytest
 
