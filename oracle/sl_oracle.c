@@ -32,6 +32,12 @@
  *   - Order reduction is isotropic and per field: m drops while any flag lies in [c-m, c+m+1]^d.
  *   - Velocity is evaluated at unwrapped positions; sin(pi x)/cos(pi x) use an exact argument
  *     reduction so that stagnation lines give exact zeros.
+ *   - Shallow water: each step starts with the nodes on the reference grid and ends with one remap;
+ *     a stage's differences are taken on the node lattice (the Z-spline derivative at the nodes:
+ *     second order for m_max <= 1, fourth order for m_max = 2) and made physical through the
+ *     inverse Jacobian of the node positions; f = f0 x2 at the node's current position; with
+ *     viscosity the stress (1 + h)(grad u + grad u^T) is formed at every node first and its
+ *     divergence taken by the same differences.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (see oracle.py).  Threads only split the
  * loop over independent target nodes; results do not depend on the thread count.
