@@ -169,3 +169,45 @@ def test_3d_shift_reproduces_polynomials(oracle_mod, m, deg):
     sl = slice(m + 3, n - m - 3)
     expect = p(kx - delta[0], ky - delta[1], kz - delta[2])
     assert np.max(np.abs(out.h[0][sl, sl, sl] - expect[sl, sl, sl])) <= 1e-12 * np.max(np.abs(expect))
+
+
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_random_affine_grids_reproduce_polynomials(oracle_mod, m):
+    """Randomised: under an affine displacement D(X) = b + S X (cell units) the element maps are
+    affine, so the logical coordinate of target x is s = (I + S)^-1 (x - b) in closed form, and
+    eq. (multiZ) must return p(s) for every p of degree <= 2m per axis (moment property (b)),
+    at every order m and on random such grids (targets whose departure point and search stay clear of
+    the periodic seam, where an affine D is not periodic)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    n = 20
+
+    @hyp.settings(max_examples=20, deadline=None, derandomize=True)
+    @hyp.given(b=st.tuples(st.floats(-2.0, 2.0), st.floats(-2.0, 2.0)),
+               S=st.tuples(*[st.floats(-0.15, 0.15)] * 4), seed=st.integers(0, 2 ** 31 - 1))
+    def check(b, S, seed):
+        A = np.array([[1.0 + S[0], S[1]], [S[2], 1.0 + S[3]]])
+        ky, kx = np.mgrid[0:n, 0:n].astype(float)
+        D = np.stack([b[0] + S[0] * kx + S[1] * ky, b[1] + S[2] * kx + S[3] * ky], axis=-1)
+        deg = max(1, 2 * m)
+        rng = np.random.default_rng(seed)
+        coef = rng.uniform(-1, 1, (deg + 1, deg + 1)) / 10.0 ** np.add.outer(np.arange(deg + 1), np.arange(deg + 1))
+
+        def p(sx, sy):
+            return sum(coef[a, c] * sx ** a * sy ** c for a in range(deg + 1) for c in range(deg + 1))
+
+        g = oracle_mod.OracleGrid(dim=2, n=(n, n), max_order=m, threshold=-1.0)
+        out = oracle_mod.remap(g, D, np.zeros((n, n), np.uint8), p(kx, ky)[None])
+        Ai = np.linalg.inv(A)
+        sx = Ai[0, 0] * (kx - b[0]) + Ai[0, 1] * (ky - b[1])
+        sy = Ai[1, 0] * (kx - b[0]) + Ai[1, 1] * (ky - b[1])
+        lo, hi = m + 3, n - m - 4
+        inner = (sx >= lo) & (sx <= hi) & (sy >= lo) & (sy <= hi) & (kx >= lo) & (kx <= hi) & (ky >= lo) & (ky <= hi)
+        hyp.assume(inner.sum() >= 4)
+        expect = p(sx, sy)
+        scale = max(1.0, float(np.abs(expect[inner]).max()))
+        assert np.all(out.status[inner] == oracle_mod.OK)
+        assert np.max(np.abs(out.h[0][inner] - expect[inner])) <= 1e-12 * scale
+
+    check()
