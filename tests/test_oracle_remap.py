@@ -171,41 +171,42 @@ def test_3d_shift_reproduces_polynomials(oracle_mod, m, deg):
     assert np.max(np.abs(out.h[0][sl, sl, sl] - expect[sl, sl, sl])) <= 1e-12 * np.max(np.abs(expect))
 
 
-@pytest.mark.parametrize("m", [0, 1, 2])
-def test_random_affine_grids_reproduce_polynomials(oracle_mod, m):
+@pytest.mark.parametrize("dim,m", [(2, 0), (2, 1), (2, 2), (3, 1), (3, 2)])
+def test_random_affine_grids_reproduce_polynomials(oracle_mod, dim, m):
     """Randomised: under an affine displacement D(X) = b + S X (cell units) the element maps are
     affine, so the logical coordinate of target x is s = (I + S)^-1 (x - b) in closed form, and
     eq. (multiZ) must return p(s) for every p of degree <= 2m per axis (moment property (b)),
-    at every order m and on random such grids (targets whose departure point and search stay clear of
-    the periodic seam, where an affine D is not periodic)."""
+    at every order m and on random such grids (targets whose departure point and search stay
+    clear of the periodic seam, where an affine D is not periodic)."""
     hyp = pytest.importorskip("hypothesis")
     st = hyp.strategies
+    n = 20 if dim == 2 else 16
+    smax, bmax = (0.15, 2.0) if dim == 2 else (0.08, 1.5)
 
-    n = 20
-
-    @hyp.settings(max_examples=20, deadline=None, derandomize=True)
-    @hyp.given(b=st.tuples(st.floats(-2.0, 2.0), st.floats(-2.0, 2.0)),
-               S=st.tuples(*[st.floats(-0.15, 0.15)] * 4), seed=st.integers(0, 2 ** 31 - 1))
+    @hyp.settings(max_examples=20 if dim == 2 else 8, deadline=None, derandomize=True)
+    @hyp.given(b=st.tuples(*[st.floats(-bmax, bmax)] * dim), S=st.tuples(*[st.floats(-smax, smax)] * (dim * dim)),
+               seed=st.integers(0, 2 ** 31 - 1))
     def check(b, S, seed):
-        A = np.array([[1.0 + S[0], S[1]], [S[2], 1.0 + S[3]]])
-        ky, kx = np.mgrid[0:n, 0:n].astype(float)
-        D = np.stack([b[0] + S[0] * kx + S[1] * ky, b[1] + S[2] * kx + S[3] * ky], axis=-1)
+        A = np.eye(dim) + np.array(S).reshape(dim, dim)
+        k = [c.astype(float) for c in reversed(np.mgrid[tuple([slice(0, n)] * dim)])]  # k[0] = x index
+        D = np.stack([b[a] + sum((A[a, c] - (a == c)) * k[c] for c in range(dim)) for a in range(dim)], axis=-1)
         deg = max(1, 2 * m)
-        rng = np.random.default_rng(seed)
-        coef = rng.uniform(-1, 1, (deg + 1, deg + 1)) / 10.0 ** np.add.outer(np.arange(deg + 1), np.arange(deg + 1))
+        coef = np.random.default_rng(seed).uniform(-1, 1, (deg + 1,) * dim)
+        coef /= 10.0 ** sum(np.ix_(*[np.arange(deg + 1)] * dim))
 
-        def p(sx, sy):
-            return sum(coef[a, c] * sx ** a * sy ** c for a in range(deg + 1) for c in range(deg + 1))
+        def p(x):
+            return sum(cv * np.prod([x[a] ** e[a] for a in range(dim)], axis=0) for e, cv in np.ndenumerate(coef))
 
-        g = oracle_mod.OracleGrid(dim=2, n=(n, n), max_order=m, threshold=-1.0)
-        out = oracle_mod.remap(g, D, np.zeros((n, n), np.uint8), p(kx, ky)[None])
+        g = oracle_mod.OracleGrid(dim=dim, n=(n,) * dim, max_order=m, threshold=-1.0)
+        out = oracle_mod.remap(g, D, np.zeros((n,) * dim, np.uint8), p(k)[None])
         Ai = np.linalg.inv(A)
-        sx = Ai[0, 0] * (kx - b[0]) + Ai[0, 1] * (ky - b[1])
-        sy = Ai[1, 0] * (kx - b[0]) + Ai[1, 1] * (ky - b[1])
+        sdep = [sum(Ai[a, c] * (k[c] - b[c]) for c in range(dim)) for a in range(dim)]
         lo, hi = m + 3, n - m - 4
-        inner = (sx >= lo) & (sx <= hi) & (sy >= lo) & (sy <= hi) & (kx >= lo) & (kx <= hi) & (ky >= lo) & (ky <= hi)
+        inner = np.ones((n,) * dim, bool)
+        for a in range(dim):
+            inner &= (sdep[a] >= lo) & (sdep[a] <= hi) & (k[a] >= lo) & (k[a] <= hi)
         hyp.assume(inner.sum() >= 4)
-        expect = p(sx, sy)
+        expect = p(sdep)
         scale = max(1.0, float(np.abs(expect[inner]).max()))
         assert np.all(out.status[inner] == oracle_mod.OK)
         assert np.max(np.abs(out.h[0][inner] - expect[inner])) <= 1e-12 * scale
