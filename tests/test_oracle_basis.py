@@ -3,8 +3,12 @@
 Each property is fixed by the paper's definition, not by the oracle's own formula:
 interpolation at the integers, compact support, the discrete-moment conditions, C^m continuity
 with piecewise degree 2m+1 (eqs. zcontin, zpolynom), and the construction itself -- a Hermite
-interpolant whose node derivatives are centered finite differences of 2m+1 points (eq. matchder).
+interpolant whose node derivatives are centered finite differences of 2m+1 points (eq. matchder);
+and the piecewise polynomials the Appendix prints (tests/golden/zspline_appendix.txt).
 """
+import os
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -138,3 +142,34 @@ def test_sinpi_cospi_exact_points(oracle_mod):
     for x in rng.uniform(-5, 5, 100):
         assert abs(oracle_mod.sinpi(x) - np.sin(np.pi * x)) <= 4e-15
         assert abs(oracle_mod.cospi(x) - np.cos(np.pi * x)) <= 4e-15
+
+
+GOLDEN_APPENDIX = os.path.join(os.path.dirname(__file__), "golden", "zspline_appendix.txt")
+
+
+def _appendix_pieces():
+    pieces = []
+    with open(GOLDEN_APPENDIX) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            m, a, b, *coef = line.split()
+            pieces.append((int(m), int(a), int(b), [float(Fraction(c)) for c in coef]))
+    return pieces
+
+
+def test_matches_the_printed_appendix_polynomials(oracle_mod):
+    """Every piece of Z~_1 and Z~_2 equals the polynomial the Appendix prints for it (both signs
+    of x, interior points and the knots)."""
+    pieces = _appendix_pieces()
+    assert sorted((m, a) for m, a, _, _ in pieces) == [(1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+    for m, a, b, coef in pieces:
+        s = np.concatenate([np.linspace(a, b, 41), np.random.default_rng(m * 10 + a).uniform(a, b, 50)])
+        printed = np.polynomial.polynomial.polyval(s, coef)
+        for sign in (1.0, -1.0):
+            got = oracle_mod.zspline(m, sign * s)
+            assert np.max(np.abs(got - printed)) <= 1e-13, (m, a, b, sign)
+    # the cubic's second piece is printed factored
+    s = np.linspace(1.0, 2.0, 11)
+    cubic2 = [c for m, a, _, c in pieces if (m, a) == (1, 1)][0]
+    assert np.max(np.abs(np.polynomial.polynomial.polyval(s, cubic2) - 0.5 * (2 - s) ** 2 * (1 - s))) <= 1e-15
