@@ -23,3 +23,14 @@ def test_reference_arm_json_line():
     assert d["config"]["workload"] == "swirl2d_1024x1024_3fields"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under a multi-rank launch only rank 0 runs the oracle and prints; the other ranks exit 0
+    without work or output."""
+    env = dict(os.environ, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"), WORLD_SIZE="2", RANK="1",
+               LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
