@@ -98,3 +98,14 @@ def test_create_rejects_bad_workspace_without_gpu(libsl):
     assert "too small" in L.sl_last_error().decode()
     assert L.sl_status_string(sl.SL_ERR_FOLD).decode() == "folded element"
     assert L.sl_destroy_grid(None) == sl.SL_ERR_ARG
+
+
+def test_missing_library_fails_loudly(libsl, monkeypatch, tmp_path):
+    """Without libsl.so the binding raises; there is no CPU fallback behind any entry point."""
+    sl = libsl
+    monkeypatch.setattr(sl, "LIB_PATH", str(tmp_path / "libsl.so"))
+    monkeypatch.setattr(sl, "_lib", None)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        sl.lib()
+    with pytest.raises(RuntimeError, match="no fallback"):
+        sl.sl_grid_workspace_bytes(sl.make_desc(2, (16, 16), 1))
