@@ -800,7 +800,8 @@ def main():
             dist.destroy_process_group()
         return 0
     cpu = None if args.no_cpu_baseline else cpu_baseline()
-    cpu_rows = None if (args.no_cpu_baseline or args.no_extra) else cpu_oracle_rows()
+    if cpu is not None and not args.no_extra:
+        cpu["other_rows"] = cpu_oracle_rows()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -822,7 +823,6 @@ def main():
                            "algorithmic_bytes_per_launch": alg_bytes, "bytes_rule": "d T + 2 F T per node (32 B)",
                            "launch_ms": remap_ms, "advect_ms": advect_ms},
         "cpu_baseline": cpu,
-        "cpu_oracle_other_rows": cpu_rows,
         "multistep_200": multistep,
         "batched": batched,
         "batched_quintic": batched_z2,
