@@ -7,6 +7,7 @@ that should reject it.  The copy never touches the real oracle build.
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -90,15 +91,40 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(name, tmp_path):
+WORKERS = max(1, min(4, (os.cpu_count() or 1) // 2))
+
+
+def _plant_and_run(name, scratch):
+    """Build the oracle with mistake `name` planted into `scratch` and run its pin tests there:
+    (pattern found, return code, end of the output)."""
     old, new, test_file = MUTATIONS[name]
     base = open(SRC).read()
-    assert old in base, "mutation pattern no longer matches the oracle source"
-    src = tmp_path / "sl_oracle.c"
-    src.write_text(base.replace(old, new, 1))
-    env = dict(os.environ, SL_ORACLE_SOURCE=str(src), SL_ORACLE_BUILD_DIR=str(tmp_path), OMP_NUM_THREADS="4")
+    if old not in base:
+        return False, None, ""
+    src = os.path.join(scratch, "sl_oracle.c")
+    with open(src, "w") as f:
+        f.write(base.replace(old, new, 1))
+    env = dict(os.environ, SL_ORACLE_SOURCE=src, SL_ORACLE_BUILD_DIR=scratch, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join("tests", test_file)], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
-    assert r.returncode == 1, f"planted mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
+    return True, r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(request, tmp_path_factory):
+    """The selected mutation cases, run a few at a time in separate processes (each builds its own
+    copy of the oracle), so that the whole set costs about a minute."""
+    names = sorted({item.callspec.params["name"] for item in request.session.items
+                    if getattr(item, "originalname", "") == "test_planted_mistake_is_caught"})
+    dirs = {n: str(tmp_path_factory.mktemp(n)) for n in names}
+    with ThreadPoolExecutor(max_workers=WORKERS) as ex:
+        futures = {n: ex.submit(_plant_and_run, n, dirs[n]) for n in names}
+        return {n: f.result() for n, f in futures.items()}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, outcomes):
+    found, rc, out = outcomes[name]
+    assert found, "mutation pattern no longer matches the oracle source"
+    assert rc == 1, f"planted mistake '{name}' was not caught:\n{out}"
