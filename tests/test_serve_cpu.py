@@ -1,6 +1,6 @@
 """Host-side logic of the server: admission under a budget and a slot limit, FIFO and
-shortest-work-first order, release, rejection of jobs larger than the budget, and sharding of jobs
-across ranks (no GPU)."""
+shortest-work-first order, release, rejection of jobs larger than the budget, sharding of jobs
+across ranks, and which jobs share a batch lane (no GPU)."""
 import numpy as np
 
 from paper_1410_2817_gb300 import inputs
@@ -109,3 +109,35 @@ def test_trace_statistics():
     frac3d = np.mean([j.workload.dim == 3 for j in jobs])
     assert 0.25 < frac3d < 0.35
     assert all(1 <= j.workload.nfields <= 4 and 10 <= j.workload.steps <= 200 for j in jobs)
+
+
+def test_lanes_group_batchable_jobs_and_isolate_the_rest():
+    """2-D FP32 jobs with a given velocity and at most 4 fields share a lane per field count and
+    spline family; FP64, 3-D, wide, carried-velocity (Burgers) and shallow-water jobs get lanes of
+    their own.  The memory a job is charged grows with the shallow-water registers."""
+    import types
+
+    from paper_1410_2817_gb300 import build, sl
+    from paper_1410_2817_gb300.serve import GpuExecutor, JobState
+    build.build()
+    ex = types.SimpleNamespace(sl=sl, dtype_code=GpuExecutor.dtype_code, tile_config=0)
+
+    def key(wl, dtype="f32", jid=1):
+        return GpuExecutor._lane_key(ex, JobState(job=inputs.Job(jid, 0.0, wl, dtype), nbytes=0))
+
+    cubic = inputs.workload_swirl(64)
+    quintic = inputs.workload_swirl(64)
+    quintic.max_order = 2
+    wide = inputs.workload_swirl(64)
+    wide.nfields, wide.fields = 5, np.zeros((5, 64, 64))
+    assert key(cubic) == ("batch", 3, False) and key(quintic) == ("batch", 3, True)
+    assert key(cubic, "f64", 7) == ("job", 7)
+    assert key(wide, jid=8) == ("job", 8)
+    assert key(inputs.workload_deform3d(16, steps=2), jid=9) == ("job", 9)
+    assert key(inputs.workload_burgers(64), jid=10) == ("job", 10)
+    assert key(inputs.workload_kelvin(64), jid=11) == ("job", 11)
+    plain = inputs.workload_swirl(64)
+    kelvin = inputs.workload_kelvin(64)
+    b_plain = GpuExecutor.bytes_of(ex, inputs.Job(1, 0.0, plain, "f32"))
+    b_kelvin = GpuExecutor.bytes_of(ex, inputs.Job(2, 0.0, kelvin, "f32"))
+    assert b_kelvin >= b_plain + 13 * 64 * 64 * 4
