@@ -211,9 +211,12 @@ sl_status sl_moments(sl_grid *grid, const void *field, int pmax, double *host_ou
  * row holds) or more than 2^31 - 1 nodes returns SL_ERR_ARG.  Every call on a device shares the
  * array and leaves its contents behind; each call overwrites everything it reads, so nothing
  * needs clearing, but calls whose kernels overlap on the GPU (different streams, no ordering)
- * race on it and must be serialised by the caller.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current) and caches it; make
- * that first call before any stream capture. */
+ * race on it and must be serialised by the caller.  The array's device address is looked up
+ * (cudaGetSymbolAddress, with the device current) on every call made outside stream capture, so
+ * a reset of the device's primary context between calls is harmless; a call made while `stream`
+ * is being captured reuses the address the last uncaptured call on that device found, so make at
+ * least one call on each device before capturing one (otherwise SL_ERR_CUDA).  A rejected call
+ * leaves its reason in sl_last_error(). */
 sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], const double hi[3], int dtype,
                              const void *field, int pmax, double *host_out, void *stream);
 

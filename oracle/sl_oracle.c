@@ -524,6 +524,13 @@ int or_locate(const or_grid *g, const double *D, const int64_t j[3], int64_t c[3
     }
     *hops = 0;
     *iters = 0;
+    /* The next element of the walk depends on the current element alone, so a walk that comes
+     * back to an element it has already tried goes round that cycle until walk_max and fails.
+     * Brent's cycle test stops it at the first repeat: `seen` is the element reached after
+     * 1, 2, 4, 8, ... hops and every later element is compared with it.  The status is the one
+     * the exhausted walk would return (OR_LOCATE). */
+    int64_t seen[3] = {c[0], c[1], c[2]};
+    int power = 1, lam = 0;
     for (int hop = 0; hop < g->walk_max; ++hop) {
         int it = 0;
         element_vertices(g, D, j, c, P);
@@ -540,6 +547,12 @@ int or_locate(const or_grid *g, const double *D, const int64_t j[3], int64_t c[3
         for (int a = 0; a < d; ++a) {
             if (xi[a] < -g->slack) c[a] -= 1;
             else if (xi[a] > 1.0 + g->slack) c[a] += 1;
+        }
+        if (c[0] == seen[0] && c[1] == seen[1] && c[2] == seen[2]) return OR_LOCATE;
+        if (++lam == power) {
+            for (int a = 0; a < 3; ++a) seen[a] = c[a];
+            power *= 2;
+            lam = 0;
         }
     }
     return OR_LOCATE;

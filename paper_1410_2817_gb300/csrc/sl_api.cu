@@ -88,7 +88,8 @@ static const char *check_desc(const sl_grid_desc *d)
         if (np != 0 && np != d->dim) return "carried velocity takes no parameter or one field index per axis";
         if (np == 0 && d->nfields < d->dim) return "carried velocity needs dim fields";
         for (int a = 0; a < np; ++a) {
-            if (!isfinite(p[a]) || p[a] != (double)(int)p[a] || p[a] < 0 || p[a] >= d->nfields)
+            // range first: the integer test converts to int only once p[a] is known to fit
+            if (!isfinite(p[a]) || p[a] < 0 || p[a] >= d->nfields || p[a] != floor(p[a]))
                 return "carried velocity field indices must be integers in [0, nfields)";
             for (int b = 0; b < a; ++b)
                 if (p[b] == p[a]) return "carried velocity field indices must be distinct";
@@ -477,6 +478,7 @@ extern "C" sl_status sl_moments(sl_grid *g, const void *field, int pmax, double 
     if (!g) return fail_arg("grid is NULL");
     if (!field || !host_out) return fail_arg("field or host_out is NULL");
     if (pmax < 0 || pmax > 7) return fail_arg("pmax must be in [0, 7]");
+    if (((uintptr_t)field % g->tsize) != 0) return fail_arg("field is not aligned to its dtype");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = g->dtype == SL_F64 ? Launch<double>::moments(g, field, pmax, s)
                                        : Launch<float>::moments(g, field, pmax, s);
@@ -572,5 +574,10 @@ extern "C" const char *sl_status_string(sl_status st)
 }
 
 extern "C" const char *sl_last_error(void) { return g_last_error; }
+
+void sl_record_error(const char *what, const char *why)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, why);
+}
 
 extern "C" const char *sl_version(void) { return "libsl 0.1 (sm_103a)"; }

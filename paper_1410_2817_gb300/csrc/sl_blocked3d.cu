@@ -141,6 +141,8 @@ __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D
     const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(SL_NEWTON_TOL_F32);
     const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(SL_SLACK_F32);
     const long long sy = g.n0, sz = (long long)g.n0 * g.n1;
+    CycleCheck cyc;
+    cyc.start(c[0], c[1], c[2]);
     for (int hop = 0; hop < walk_max; ++hop) {
         TN P[8][3];
         float4 d8[8];
@@ -186,6 +188,7 @@ __device__ __forceinline__ int walk3(const Geo3 &g, const float4 *__restrict__ D
             else if (xi[a] > TN(1) + slack)
                 c[a] += 1;
         }
+        if (cyc.step(c[0], c[1], c[2])) return ST_LOCATE;
     }
     return ST_LOCATE;
 }

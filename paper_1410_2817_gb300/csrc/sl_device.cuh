@@ -502,6 +502,36 @@ __device__ __forceinline__ void zs_weights(int m, T xi, T w[6])
     for (int k = 0; k < 6; ++k) w[k] = (k < 2 * m + 2) ? zspline<T>(m, T(m - k) + xi) : T(0);
 }
 
+// Sec. 2.2 element search: the next element depends on the current element alone, so a walk that
+// returns to an element it has already tried cycles until its hop limit and fails.  Brent's cycle
+// test stops it at the first repeat: `seen` holds the element reached after 1, 2, 4, 8, ... hops
+// and every later element is compared with it.  step() is called after each move and returns true
+// when the walk has come back to `seen` (the caller then gives up with ST_LOCATE, the status the
+// exhausted walk would return).
+struct CycleCheck {
+    int s0, s1, s2, power, lam;
+    __device__ __forceinline__ void start(int c0, int c1, int c2)
+    {
+        s0 = c0;
+        s1 = c1;
+        s2 = c2;
+        power = 1;
+        lam = 0;
+    }
+    __device__ __forceinline__ bool step(int c0, int c1, int c2)
+    {
+        if (c0 == s0 && c1 == s1 && c2 == s2) return true;
+        if (++lam == power) {
+            s0 = c0;
+            s1 = c1;
+            s2 = c2;
+            power <<= 1;
+            lam = 0;
+        }
+        return false;
+    }
+};
+
 // Sec. 2.3 jump test of one node along one axis.
 template <typename T>
 __device__ __forceinline__ bool jump_test(T hm, T h0, T hp, T thr)

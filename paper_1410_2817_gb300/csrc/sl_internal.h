@@ -102,6 +102,9 @@ cudaError_t launch_tiled2d_z2(const sl_grid *g, const void *D, void *D_next, dou
                               const void *const *in, void *const *out, cudaStream_t s);
 size_t tiled2d_smem_bytes_z2(int nfields);
 
+// the text sl_last_error() returns for this thread's last failed call (sl_api.cu)
+void sl_record_error(const char *what, const char *why);
+
 // shared argument builders (sl_kernels.cu)
 template <typename T>
 GridArgs<T> make_grid_args(const sl_grid *g);

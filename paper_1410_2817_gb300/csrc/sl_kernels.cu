@@ -242,6 +242,8 @@ __device__ __forceinline__ int walk_global(const WalkParams<TN> &w, const int n[
                                            const int j[3], int c[3], TN xi[3], int *hops, int *iters,
                                            bool *degenerate = nullptr)
 {
+    CycleCheck cyc;
+    cyc.start(c[0], c[1], c[2]);
     for (int hop = 0; hop < w.walk_max; ++hop) {
         TN P[8][3];
 #pragma unroll
@@ -272,6 +274,7 @@ __device__ __forceinline__ int walk_global(const WalkParams<TN> &w, const int n[
             else if (xi[a] > TN(1) + w.slack)
                 c[a] += 1;
         }
+        if (cyc.step(c[0], c[1], c[2])) return ST_LOCATE;
     }
     return ST_LOCATE;
 }

@@ -12,30 +12,39 @@
 static __device__ __align__(256) double g_noalloc_scratch[SL_MOMENT_BLOCKS * 8 + 8];
 
 // Device address of the scratch array on the current device.  The host-side name of a
-// __device__ variable is only a stand-in, so the address is looked up once per device (with that
-// device current) and cached.
-static cudaError_t scratch_address(int device, double **out)
+// __device__ variable is only a stand-in, so the address is looked up with that device current.
+// Outside stream capture it is looked up on every call (a cheap table lookup once the module is
+// loaded), so that a reset of the device's primary context between calls, which moves the array,
+// is picked up; the last address seen on each device is kept for calls made while `s` is being
+// captured, where no lookup is made.  A first call on a device inside a capture therefore fails
+// with cudaErrorStreamCaptureUnsupported.
+static cudaError_t scratch_address(int device, cudaStream_t s, double **out)
 {
     static std::mutex mu;
     static double *addr[64];
     static bool ready[64];
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
-    if (!ready[device]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         double *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         addr[device] = p;
         ready[device] = true;
+    } else if (!ready[device]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = addr[device];
     return cudaSuccess;
 }
 
-// the reason is for a reader of this file; callers see the status code only
+// record the reason where sl_last_error() finds it, as every other entry point does
 static sl_status noalloc_fail(sl_status st, const char *why)
 {
-    (void)why;
+    sl_record_error(st == SL_ERR_ARG ? "sl_moments_noalloc: invalid argument" : "sl_moments_noalloc", why);
     return st;
 }
 
@@ -60,7 +69,7 @@ extern "C" sl_status sl_moments_noalloc(int dim, const int64_t n[3], const doubl
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     double *scratch = nullptr;
-    if (e == cudaSuccess) e = scratch_address(device, &scratch);
+    if (e == cudaSuccess) e = scratch_address(device, (cudaStream_t)stream, &scratch);
     if (e != cudaSuccess) return noalloc_fail(SL_ERR_CUDA, cudaGetErrorString(e));
 
     // a host-side grid object that carries only what the moments launcher reads

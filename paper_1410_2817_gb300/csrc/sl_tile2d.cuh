@@ -104,6 +104,8 @@ __device__ __forceinline__ int walk2(const TileArgs &a, const Win &w, const floa
 {
     const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(SL_NEWTON_TOL_F32);
     const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(SL_SLACK_F32);
+    CycleCheck cyc;
+    cyc.start(cx, cy, 0);
     for (int hop = 0; hop < a.walk_max; ++hop) {
         TN P[8][3];
         float2 d4[4];
@@ -137,6 +139,7 @@ __device__ __forceinline__ int walk2(const TileArgs &a, const Win &w, const floa
             cy -= 1;
         else if (xi[1] > TN(1) + slack)
             cy += 1;
+        if (cyc.step(cx, cy, 0)) return ST_LOCATE;
     }
     return ST_LOCATE;
 }
@@ -150,6 +153,8 @@ __device__ __forceinline__ bool walk_window(const Win &w, const float2 *sD, int 
                                             int &ex, int &ey, float &xi0, float &xi1, int &hops, int &iters)
 {
     const float slack = SL_SLACK_F32;
+    CycleCheck cyc;
+    cyc.start(ex, ey, 0);
     for (int hop = 0; hop < walk_max; ++hop) {
         if (!(w.has(ex, ey) && w.has(ex + 1, ey + 1))) return false;
         const int i0 = w.at(ex, ey);
@@ -181,6 +186,7 @@ __device__ __forceinline__ bool walk_window(const Win &w, const float2 *sD, int 
         }
         ex += lo0 ? -1 : (hi0 ? 1 : 0);
         ey += lo1 ? -1 : (hi1 ? 1 : 0);
+        if (cyc.step(ex, ey, 0)) return false;
     }
     return false;
 }

@@ -323,6 +323,28 @@ def test_moments_parity_and_table1(sl, orc):
 # ------------------------------------------------------------------------------------------------
 # failure reporting and argument errors through the ABI
 # ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_cycling_walks_stop_early(sl, orc, dtype):
+    """Sec. 2.2: a walk that returns to an element it has tried gives up at once (the next element
+    depends on the current one alone).  On the 64x64 solid-body rotation the seam's failing
+    targets are exactly the oracle's, and no walk -- FP32 or its FP64 re-solve -- runs to the
+    64-hop limit."""
+    wl = inputs.workload_sbr64()
+    og = _og(orc, 2, wl.n, 1, velocity=wl.velocity, params=wl.velocity_params)
+    D = orc.advect(og, 0.0, wl.dt)
+    ref = orc.remap(og, D, orc.flags(og, wl.fields), wl.fields)
+    nfail = int((ref.status != orc.OK).sum())
+    assert nfail > 0
+    sd, td = (sl.SL_F64, torch.float64) if dtype == "f64" else (sl.SL_F32, torch.float32)
+    g = sl.grid_for(wl, sd)
+    f = torch.tensor(wl.fields, dtype=td, device=DEV)
+    g.set_displacement(torch.tensor(D, dtype=td, device=DEV))
+    g.remap(f, torch.empty_like(f))
+    d = g.diagnostics()
+    assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == nfail
+    assert d["hops_max"] < 32, d
+
+
 def test_fail_error_policy_reports(sl, orc):
     wl = inputs.workload_sbr64()
     g = sl.grid_for(wl, sl.SL_F64, fail_policy=sl.SL_FAIL_ERROR)

@@ -183,3 +183,55 @@ def test_walk_gives_up(oracle_mod):
     g = oracle_mod.OracleGrid(dim=2, n=(n, n), walk_max=3)
     _, _, st, hops, _ = oracle_mod.locate(g, D, (7, 7))
     assert st == oracle_mod.LOCATE and hops == 3
+
+
+def _replay_walk(oracle_mod, g, D, j, c0, walk_max):
+    """The walk of Sec. 2.2 replayed step by step with no revisit rule: invert in the current
+    element and step one element along every axis whose local coordinate is out of range.
+    Returns (status, hops, elements tried)."""
+    d = g.dim
+    n = np.array(g.n[:d])
+    c = np.array(c0, dtype=np.int64)
+    tried = []
+    for hop in range(walk_max):
+        P = []
+        for v in range(1 << d):
+            k = c + np.array([(v >> a) & 1 for a in range(d)])
+            kw = tuple(int(x) for x in np.mod(k, n))
+            P.append(k - np.array(j) + D[kw[::-1]])
+        xi, st, _ = oracle_mod.newton(np.array(P))
+        tried.append(tuple(int(x) for x in c))
+        if not np.all(np.isfinite(xi)):
+            return ("newton" if st == oracle_mod.OK else st), hop + 1, tried
+        if np.all(xi >= -1e-12) and np.all(xi <= 1 + 1e-12):
+            return st, hop + 1, tried
+        c = c + np.where(xi < -1e-12, -1, 0) + np.where(xi > 1 + 1e-12, 1, 0)
+    return oracle_mod.LOCATE, walk_max, tried
+
+
+def test_walk_stops_on_a_revisit(oracle_mod):
+    """Sec. 2.2: the next element depends on the current one alone, so a walk that comes back to
+    an element it has tried would cycle until walk_max.  The oracle gives up at the first repeat
+    (Brent's test).  On the 64x64 solid-body rotation, whose elements sheared across the seam
+    make walks fail, every target's status equals that of the walk replayed without the rule for
+    the full 64 hops; every failure is such a cycle and is found within a few hops; and the
+    targets that succeed take exactly the replay's hops."""
+    wl = inputs.workload_sbr64()
+    g = oracle_mod.OracleGrid(dim=2, n=wl.n, nfields=1, velocity=wl.velocity, velocity_params=wl.velocity_params)
+    D = oracle_mod.advect(g, 0.0, wl.dt)
+    nfail = 0
+    for jy in range(wl.n[1]):
+        for jx in range(wl.n[0]):
+            j = (jx, jy)
+            c0 = (jx - (1 if D[jy, jx, 0] > 0 else 0), jy - (1 if D[jy, jx, 1] > 0 else 0))
+            c, xi, st, hops, _ = oracle_mod.locate(g, D, j)
+            rst, rhops, tried = _replay_walk(oracle_mod, g, D, j, c0, 64)
+            assert st == rst, (j, st, rst)
+            if st == oracle_mod.LOCATE:
+                nfail += 1
+                assert len(set(tried)) < len(tried), j  # the replayed walk revisits an element
+                first_repeat = next(k for k in range(len(tried)) if tried[k] in tried[:k])
+                assert hops <= 3 * first_repeat + 2 and hops < 64, (j, hops, first_repeat)
+            else:
+                assert hops == rhops, (j, hops, rhops)
+    assert nfail > 0

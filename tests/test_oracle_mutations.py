@@ -82,6 +82,10 @@ MUTATIONS = {
     "nlsw_stage_weight": ("B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};", "B[3] = {1.0 / 3.0, 0.5, 8.0 / 15.0};",
                           "test_oracle_nlsw.py"),
     "step_time": ("double t = t0 + (double)s * dt;", "double t = t0;", "test_oracle_step.py"),
+    "walk_revisit_one_axis": ("if (c[0] == seen[0] && c[1] == seen[1] && c[2] == seen[2]) return OR_LOCATE;",
+                              "if (c[0] == seen[0]) return OR_LOCATE;", "test_oracle_mapping.py"),
+    "walk_revisit_never_moves": ("for (int a = 0; a < 3; ++a) seen[a] = c[a];", "(void)0;",
+                                 "test_oracle_mapping.py"),
     "cramer_column": ("M[a][b] = (b == c) ? r[a] : J[a][b];", "M[a][b] = (a == c) ? r[b] : J[a][b];",
                       "test_oracle_mapping.py"),
     "moment_power": ("for (int q = 0; q < p; ++q) rp *= r;", "for (int q = 1; q < p; ++q) rp *= r;",

@@ -25,6 +25,13 @@ def sl():
     return slmod
 
 
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
 def _noalloc(sl, dim, n, lo, hi, dtype, field, pmax):
     nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     lo_ = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
@@ -36,7 +43,7 @@ def _noalloc(sl, dim, n, lo, hi, dtype, field, pmax):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_noalloc_moments_match_grid_moments(sl, dtype):
+def test_noalloc_moments_match_grid_moments(sl, orc, dtype):
     sd = sl.SL_F64 if dtype == "f64" else sl.SL_F32
     td = torch.float64 if dtype == "f64" else torch.float32
     cases = [(2, (96, 70), (0.0, -1.0), (2.0, 1.5), 4), (3, (11, 7, 9), (0.0, -1.0, 2.0), (1.0, 3.0, 4.0), 7)]
@@ -50,11 +57,16 @@ def test_noalloc_moments_match_grid_moments(sl, dtype):
             assert st == sl.SL_OK
             for a, b in zip(got, ref):
                 assert abs(a - b) <= 1e-13 * max(1.0, abs(b)), (dim, call, a, b)
+            # and against the oracle's moments of the same plane
+            og = orc.OracleGrid(dim=dim, n=n, nfields=1, lo=lo, hi=hi)
+            for a, b in zip(got, orc.moments(og, field.double().cpu().numpy(), pmax)):
+                assert abs(a - b) <= 1e-12 * max(1.0, abs(b)), (dim, call, a, b)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(sl):
     field = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
     st, _ = _noalloc(sl, 2, (8, 8), (0, 0), (1, 1), sl.SL_F64, field, 8)
     assert st == sl.SL_ERR_ARG
+    assert "pmax" in sl.lib().sl_last_error().decode()
     st, _ = _noalloc(sl, 2, (1 << 16, 1 << 16), (0, 0), (1, 1), sl.SL_F64, field, 2)
     assert st == sl.SL_ERR_ARG
