@@ -235,6 +235,22 @@ def fourier_speed_bound(params: Sequence[float], dim: int) -> float:
     return s
 
 
+def fourier2d_max_speed(params: Sequence[float], n: int) -> float:
+    """Largest speed |u| of a 2-D Fourier velocity over the nodes of an n x n grid of the unit
+    square (u = d psi/dy, v = -d psi/dx of psi = sum a cos(2 pi k.x) + b sin(2 pi k.x))."""
+    x, y = node_coords((n, n))
+    u = np.zeros_like(x)
+    v = np.zeros_like(x)
+    nm = int(params[0])
+    for q in range(nm):
+        kx, ky, a, b = params[1 + 4 * q: 5 + 4 * q]
+        th = 2.0 * math.pi * (kx * x + ky * y)
+        dpsi = 2.0 * math.pi * (b * np.cos(th) - a * np.sin(th))
+        u += ky * dpsi
+        v -= kx * dpsi
+    return float(np.sqrt(u * u + v * v).max())
+
+
 def gaussian_and_step_2d(n: int) -> np.ndarray:
     x, y = node_coords((n, n))
     g = np.exp(-(_min_image(x - 0.3) ** 2 + _min_image(y - 0.3) ** 2) / (2 * 0.1 ** 2))
@@ -246,14 +262,15 @@ def batched_grids(count: int = 512, seed: int = 0, steps: int = 50, cfl: float =
                   side_lo: int = 32, side_hi: int = 512, with_fields: bool = True) -> List[Workload]:
     """Independent 2-D periodic grids with sides log-uniform in [side_lo, side_hi], each with a
     steady divergence-free velocity from a random streamfunction of 8 Fourier modes
-    (wavenumbers 1-4, N(0,1) amplitudes), a Gaussian and a step field; dt = cfl*dx/max|u|."""
+    (wavenumbers 1-4, N(0,1) amplitudes), a Gaussian and a step field; dt = cfl*dx/max|u|, the
+    largest speed taken over the grid's nodes."""
     rng = np.random.default_rng(seed)
     sides = np.round(np.exp(rng.uniform(math.log(side_lo), math.log(side_hi), size=count))).astype(int)
     out = []
     for g, nside in enumerate(sides):
         r = np.random.default_rng([seed, g])
         p = fourier2d_params(r)
-        vmax = fourier_speed_bound(p, 2)
+        vmax = fourier2d_max_speed(p, int(nside))
         dt = cfl / (nside * vmax)
         out.append(Workload(f"batch{g}_{nside}", 2, (int(nside), int(nside)), 2, "fourier2d", p, dt, steps,
                             fields=gaussian_and_step_2d(int(nside)) if with_fields else None))
