@@ -327,8 +327,8 @@ def test_moments_parity_and_table1(sl, orc):
 def test_cycling_walks_stop_early(sl, orc, dtype):
     """Sec. 2.2: a walk that returns to an element it has tried gives up at once (the next element
     depends on the current one alone).  On the 64x64 solid-body rotation the seam's failing
-    targets are exactly the oracle's, and no walk -- FP32 or its FP64 re-solve -- runs to the
-    64-hop limit."""
+    targets are exactly the oracle's, and all the walks of a target together -- FP32 and its FP64
+    re-solve -- take fewer hops than one walk run to the 64-hop limit."""
     wl = inputs.workload_sbr64()
     og = _og(orc, 2, wl.n, 1, velocity=wl.velocity, params=wl.velocity_params)
     D = orc.advect(og, 0.0, wl.dt)
@@ -342,7 +342,9 @@ def test_cycling_walks_stop_early(sl, orc, dtype):
     g.remap(f, torch.empty_like(f))
     d = g.diagnostics()
     assert d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == nfail
-    assert d["hops_max"] < 32, d
+    # hops_max adds up every walk a target made (FP32 in the window, FP32 from global memory, the
+    # FP64 re-solve); before the revisit rule one exhausted walk alone took 64
+    assert d["hops_max"] < 64, d
 
 
 def test_fail_error_policy_reports(sl, orc):
