@@ -121,10 +121,16 @@ typedef struct {
     int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
     int walk_start;                 /* SL_START_BACKWARD (from j - D_j) or SL_START_PAPER (Sec. 2.2) */
     int kernel;                     /* SL_KERNEL_AUTO, SL_KERNEL_GENERIC or SL_KERNEL_TILED           */
-    int tile_config;                /* 2-D FP32 tiles: 0 default (= 1), 1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16
-                                       compiled for 4 CTAs per SM, 5: 32x32 pipelined (persistent,
-                                       one CTA per SM staging the next tiles while it computes;
-                                       1 above 4 fields; batches run 5 as 1)                      */
+    int tile_config;                /* 2-D FP32 tiles: 0 default (7 where it applies, else 1);
+                                       6: 64x32 and 7: 32x32 tiles of the persistent kernel whose
+                                       windows are copied by TMA boxes (one CTA per SM with 6, two
+                                       with 7; up to 3 fields, max_order <= 1, an analytic velocity,
+                                       even n[0], 16-byte aligned planes, else 1);
+                                       1: 32x32, 2: 32x16, 3: 64x16, 4: 32x16 compiled for 4 CTAs
+                                       per SM, 5: 32x32 pipelined (persistent, one CTA per SM
+                                       staging the next tiles while it computes; 1 above 4
+                                       fields) -- the shared-memory tile kernels with per-element
+                                       copies.  Batches take their own tile configuration (0..5). */
     int trajectory_substeps;        /* integrator steps per remap (Sec. 2: the Lagrangian grid may
                                        move for several time steps before the fields are
                                        interpolated back): each step of length dt integrates the
@@ -144,6 +150,8 @@ typedef struct {
     uint64_t order_hist[3];         /* field-targets interpolated with order 0, 1, 2                 */
     uint64_t tiles_fallback;        /* tiles whose stencil window did not fit shared memory          */
     uint64_t kernel_launches;       /* kernels this grid's calls have launched (host-side count)    */
+    uint64_t timeouts;              /* bounded waits for shared-memory copies that ran out (the CTA
+                                       stopped; its targets are left unwritten) -- expected 0      */
 } sl_diag;
 
 /* Remap debug outputs (device pointers, each may be NULL). */
@@ -192,6 +200,15 @@ sl_status sl_remap_fields_debug(sl_grid *grid, const void *const *in, void *cons
  * next call starting there with the same dt does not integrate it again. */
 sl_status sl_step(sl_grid *grid, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
                   void *stream);
+
+/* The same steps out of place: `in` (nfields device planes, read only) is advanced nsteps steps
+ * and the result written to `out`; `scratch` (nfields planes) is the other half of the ping-pong
+ * for nsteps > 1 and may be NULL for nsteps <= 1.  in, out and scratch must not overlap.  One step
+ * on the fused FP32 path is one launch, with no copy back (a shallow-water grid copies `in` to
+ * `out` first and advances it in place).  The carried displacement and SL_FAIL_ERROR behave as
+ * in sl_step. */
+sl_status sl_step_out(sl_grid *grid, const void *const *in, void *const *out, void *const *scratch, double t0, double dt,
+                      int nsteps, void *stream);
 
 /* Sec. 3.1: discrete moments of one field plane about the box centre c:
  * m_0 = sum h,  m_p = sum_i h_i sum_a (x_a^i - c_a)^p for 1 <= p <= pmax (<= 7), accumulated in

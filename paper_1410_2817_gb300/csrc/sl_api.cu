@@ -53,7 +53,7 @@ static const char *check_desc(const sl_grid_desc *d)
     if (d->fail_policy != SL_FAIL_KEEP && d->fail_policy != SL_FAIL_ERROR) return "bad fail_policy";
     if (d->walk_start != SL_START_BACKWARD && d->walk_start != SL_START_PAPER) return "bad walk_start";
     if (d->kernel < SL_KERNEL_AUTO || d->kernel > SL_KERNEL_TILED) return "bad kernel";
-    if (d->tile_config < 0 || d->tile_config > 5) return "tile_config must be in [0, 5]";
+    if (d->tile_config < 0 || d->tile_config > 7) return "tile_config must be in [0, 7]";
     if (d->newton_max_iter > 64 || d->walk_max > 4096) return "newton_max_iter <= 64 and walk_max <= 4096";
     const int np = d->n_velocity_params;
     if (np < 0 || np > SL_MAX_VEL_PARAMS) return "n_velocity_params out of range";
@@ -321,27 +321,41 @@ static sl_status read_counters(sl_grid *g, DevCounters *c, cudaStream_t s)
     return SL_OK;
 }
 
+// nsteps full steps.  Step k reads src_k and writes dst_k: src_0 = in, dst_0 = A, and the
+// destinations alternate A, B, A, ... (src_{k+1} = dst_k), so the result ends in A after an odd
+// number of steps and in B after an even one.  `in` is read only by the first step; B may equal
+// `in` (sl_step's in-place ping-pong).  A shallow-water grid advances `in` in place through its
+// stages and remap (A, B unused except as the stages' scratch: see below).
 template <typename T>
-static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
-                             cudaStream_t s)
+static cudaError_t step_impl(sl_grid *g, const void *const *in, void *const *A, void *const *B, double t0, double dt,
+                             int nsteps, cudaStream_t s)
 {
     const void *cur[SL_MAX_FIELDS];
     void *nxt[SL_MAX_FIELDS];
     for (int q = 0; q < g->nfields; ++q) {
-        cur[q] = fields[q];
-        nxt[q] = scratch[q];
+        cur[q] = in[q];
+        nxt[q] = A[q];
     }
+    // after a step: its destination is the next source, the other buffer the next destination
+    auto advance = [&]() {
+        const bool wasA = nxt[0] == A[0];
+        for (int q = 0; q < g->nfields; ++q) {
+            cur[q] = nxt[q];
+            nxt[q] = wasA ? B[q] : A[q];
+        }
+    };
     cudaError_t e = cudaSuccess;
     if (g->nlsw) {
-        // the three RK3 stages on the nodes (four launches; the node values end in the scratch
-        // planes), then the remap back into the caller's planes: the result lands in `fields`
-        // after every step
+        // the three RK3 stages on the nodes (four launches; the node values end in A), then the
+        // remap back into `in`'s planes: the result lands in `in` after every step (the caller
+        // passes writable planes there)
         g->d_cached = 0;
         g->next_valid = 0;
+        void *const *fields = (void *const *)in;
         for (int k = 0; k < nsteps; ++k) {
-            e = counted(g, Launch<T>::nlsw_stages(g, (const void *const *)fields, scratch, g->D[g->dcur],
-                                                  g->D[g->dcur ^ 1], dt, s), nlsw_kernels_per_step(g));
-            if (e == cudaSuccess) e = remap_impl<T>(g, g->D[g->dcur], (const void *const *)scratch, fields, nullptr, s);
+            e = counted(g, Launch<T>::nlsw_stages(g, in, A, g->D[g->dcur], g->D[g->dcur ^ 1], dt, s),
+                        nlsw_kernels_per_step(g));
+            if (e == cudaSuccess) e = remap_impl<T>(g, g->D[g->dcur], (const void *const *)A, fields, nullptr, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -364,14 +378,9 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
                         tiled_kernels_per_call(g));
             if (e != cudaSuccess) return e;
             if (dnext) g->dcur = nx;
-            for (int q = 0; q < g->nfields; ++q) {
-                void *tmp = nxt[q];
-                nxt[q] = (void *)cur[q];
-                cur[q] = tmp;
-            }
+            advance();
         }
-        if (nsteps % 2 == 1) e = counted(g, Launch<T>::copy_planes(g, cur, fields, s), 1);
-        return e;
+        return cudaSuccess;
     }
     // otherwise a carried velocity is read from the fields at the start of each step by its own
     // launch before the remap
@@ -430,18 +439,35 @@ static cudaError_t step_impl(sl_grid *g, void *const *fields, void *const *scrat
                 e = counted(g, Launch<T>::remap_generic(g, g->D[g->dcur], g->flags, cur, nxt, nullptr, s), 1);
             if (e != cudaSuccess) return e;
         }
-        for (int q = 0; q < g->nfields; ++q) {
-            void *tmp = nxt[q];
-            nxt[q] = (void *)cur[q];
-            cur[q] = tmp;
-        }
-    }
-    if (nsteps % 2 == 1) {
-        // the result sits in the scratch planes: copy every plane back in one launch
-        e = counted(g, Launch<T>::copy_planes(g, cur, fields, s), 1);
-        if (e != cudaSuccess) return e;
+        advance();
     }
     return cudaSuccess;
+}
+
+static sl_status check_step_args(const sl_grid *g, int nsteps, double t0, double dt)
+{
+    if (nsteps < 0) return fail_arg("nsteps must be >= 0");
+    if (!isfinite(t0) || !isfinite(dt)) return fail_arg("t0 and dt must be finite");
+    return SL_OK;
+}
+
+static bool planes_overlap(const sl_grid *g, const void *const *a, const void *const *b)
+{
+    for (int q = 0; q < g->nfields; ++q)
+        for (int r = 0; r < g->nfields; ++r)
+            if (a[q] == b[r]) return true;
+    return false;
+}
+
+// counters before the call (SL_FAIL_ERROR) and the failure status after it
+static sl_status fail_policy_result(sl_grid *g, const DevCounters &before, cudaStream_t s)
+{
+    DevCounters after;
+    if (sl_status st = read_counters(g, &after, s)) return st;
+    if (after.fail_locate > before.fail_locate) return SL_ERR_LOCATE;
+    if (after.fail_newton > before.fail_newton) return SL_ERR_NEWTON;
+    if (after.fail_fold > before.fail_fold) return SL_ERR_FOLD;
+    return SL_OK;
 }
 
 extern "C" sl_status sl_step(sl_grid *g, void *const *fields, void *const *scratch, double t0, double dt, int nsteps,
@@ -450,26 +476,66 @@ extern "C" sl_status sl_step(sl_grid *g, void *const *fields, void *const *scrat
     if (!g) return fail_arg("grid is NULL");
     if (sl_status st = check_planes(g, (const void *const *)fields, "field planes")) return st;
     if (sl_status st = check_planes(g, (const void *const *)scratch, "scratch planes")) return st;
-    for (int q = 0; q < g->nfields; ++q)
-        for (int r = 0; r < g->nfields; ++r)
-            if (fields[q] == scratch[r]) return fail_arg("field and scratch planes must not overlap");
-    if (nsteps < 0) return fail_arg("nsteps must be >= 0");
-    if (!isfinite(t0) || !isfinite(dt)) return fail_arg("t0 and dt must be finite");
+    if (planes_overlap(g, (const void *const *)fields, (const void *const *)scratch))
+        return fail_arg("field and scratch planes must not overlap");
+    if (sl_status st = check_step_args(g, nsteps, t0, dt)) return st;
     if (nsteps == 0) return SL_OK;
     cudaStream_t s = (cudaStream_t)stream;
     DevCounters before;
     if (g->desc.fail_policy == SL_FAIL_ERROR)
         if (sl_status st = read_counters(g, &before, s)) return st;
-    cudaError_t e = g->dtype == SL_F64 ? step_impl<double>(g, fields, scratch, t0, dt, nsteps, s)
-                                       : step_impl<float>(g, fields, scratch, t0, dt, nsteps, s);
+    // the ping-pong between scratch and the caller's planes: after an odd number of steps the
+    // result sits in the scratch planes and is copied back in one launch (a shallow-water grid
+    // ends every step in `fields` itself)
+    cudaError_t e = g->dtype == SL_F64
+                        ? step_impl<double>(g, (const void *const *)fields, scratch, fields, t0, dt, nsteps, s)
+                        : step_impl<float>(g, (const void *const *)fields, scratch, fields, t0, dt, nsteps, s);
+    if (e == cudaSuccess && !g->nlsw && nsteps % 2 == 1)
+        e = counted(g, g->dtype == SL_F64 ? Launch<double>::copy_planes(g, (const void *const *)scratch, fields, s)
+                                          : Launch<float>::copy_planes(g, (const void *const *)scratch, fields, s),
+                    1);
     if (e != cudaSuccess) return fail_cuda(e, "sl_step");
-    if (g->desc.fail_policy == SL_FAIL_ERROR) {
-        DevCounters after;
-        if (sl_status st = read_counters(g, &after, s)) return st;
-        if (after.fail_locate > before.fail_locate) return SL_ERR_LOCATE;
-        if (after.fail_newton > before.fail_newton) return SL_ERR_NEWTON;
-        if (after.fail_fold > before.fail_fold) return SL_ERR_FOLD;
+    if (g->desc.fail_policy == SL_FAIL_ERROR) return fail_policy_result(g, before, s);
+    return SL_OK;
+}
+
+extern "C" sl_status sl_step_out(sl_grid *g, const void *const *in, void *const *out, void *const *scratch, double t0,
+                                 double dt, int nsteps, void *stream)
+{
+    if (!g) return fail_arg("grid is NULL");
+    if (sl_status st = check_planes(g, in, "input planes")) return st;
+    if (sl_status st = check_planes(g, (const void *const *)out, "output planes")) return st;
+    if (planes_overlap(g, in, (const void *const *)out)) return fail_arg("input and output planes must not overlap");
+    const bool need_scratch = nsteps > 1 || g->nlsw;
+    if (need_scratch) {
+        if (sl_status st = check_planes(g, (const void *const *)scratch, "scratch planes")) return st;
+        if (planes_overlap(g, in, (const void *const *)scratch) ||
+            planes_overlap(g, (const void *const *)out, (const void *const *)scratch))
+            return fail_arg("scratch planes must not overlap the input or output planes");
     }
+    if (sl_status st = check_step_args(g, nsteps, t0, dt)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (nsteps == 0 || g->nlsw) {
+        // nothing to advance, or a shallow-water grid (which advances its planes in place): the
+        // input is copied to the output first
+        e = counted(g, g->dtype == SL_F64 ? Launch<double>::copy_planes(g, in, out, s)
+                                          : Launch<float>::copy_planes(g, in, out, s),
+                    1);
+        if (e != cudaSuccess) return fail_cuda(e, "sl_step_out");
+        if (nsteps == 0) return SL_OK;
+        return sl_step(g, out, scratch, t0, dt, nsteps, stream);
+    }
+    DevCounters before;
+    if (g->desc.fail_policy == SL_FAIL_ERROR)
+        if (sl_status st = read_counters(g, &before, s)) return st;
+    // destinations alternate so that the last step writes `out`
+    void *const *A = nsteps % 2 == 1 ? out : scratch;
+    void *const *B = nsteps % 2 == 1 ? scratch : out;
+    e = g->dtype == SL_F64 ? step_impl<double>(g, in, A, B, t0, dt, nsteps, s)
+                           : step_impl<float>(g, in, A, B, t0, dt, nsteps, s);
+    if (e != cudaSuccess) return fail_cuda(e, "sl_step_out");
+    if (g->desc.fail_policy == SL_FAIL_ERROR) return fail_policy_result(g, before, s);
     return SL_OK;
 }
 
@@ -547,6 +613,7 @@ extern "C" sl_status sl_get_diagnostics(sl_grid *g, sl_diag *out, void *stream)
     for (int q = 0; q < 3; ++q) out->order_hist[q] = c.order_hist[q];
     out->tiles_fallback = c.tiles_fallback;
     out->kernel_launches = g->launches;
+    out->timeouts = c.timeouts;
     return SL_OK;
 }
 

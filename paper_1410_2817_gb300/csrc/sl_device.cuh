@@ -25,6 +25,7 @@ struct DevCounters {
     unsigned long long targets, fail_locate, fail_newton, fail_fold;
     unsigned long long hops_sum, hops_max, iters_sum, iters_max;
     unsigned long long newton_f64, order_hist[3], tiles_fallback;
+    unsigned long long timeouts;  // bounded waits on shared-memory copies that ran out
 };
 
 template <typename T>

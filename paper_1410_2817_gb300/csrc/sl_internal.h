@@ -97,6 +97,11 @@ size_t tiled2d_smem_bytes_cfgd(int nfields);
 // shallow water (sl_nlsw.cu): the viscosity nu of a grid and the launches of one step's stages
 double nlsw_viscosity(const sl_grid *g);
 int nlsw_kernels_per_step(const sl_grid *g);
+// 2-D FP32 persistent remap with TMA-staged windows (sl_remap2d.cu): configuration 6 (64x32 tiles,
+// one CTA per SM) or 7 (32x32 tiles, two CTAs per SM)
+bool remap2d_tma_supported(const sl_grid *g, const void *const *in, void *const *out);
+cudaError_t launch_remap2d_tma(const sl_grid *g, int config, const void *D, void *D_next, double t_next, double dt,
+                               bool fused, const void *const *in, void *const *out, cudaStream_t s);
 // 2-D FP32 tiled kernels of the quintic Z-spline (max_order 2; sl_tiled_z2.cu)
 cudaError_t launch_tiled2d_z2(const sl_grid *g, const void *D, void *D_next, double t_next, double dt, bool fused,
                               const void *const *in, void *const *out, cudaStream_t s);

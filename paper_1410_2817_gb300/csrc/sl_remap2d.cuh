@@ -1,0 +1,694 @@
+// sl_remap2d.cuh -- persistent 2-D FP32 remap of the FSL step (arXiv:1410.2817) with TMA-staged
+// departure windows: one CTA per SM walks through TX x TY tiles of target (reference) nodes.
+//
+// Per tile (Sec. 2.2, 2.3, eq. multiZ):
+//   1. start points s = j - D_j of the tile's targets and the box of their elements floor(s);
+//   2. the departure window -- that box widened by the walk slack, the cubic stencil (c-1 .. c+2)
+//      and the limiter's neighbours -- is copied to shared memory: the displacement and the field
+//      planes by cp.async.bulk.tensor box loads (8-row strips, one mbarrier, no multicast), or by
+//      per-element asynchronous copies when the window crosses the periodic seam;
+//   3. one pass over the window computes every node's jump flags (Sec. 2.3) and rewrites the
+//      planar field values as float4 records (h0, h1, h2, flag bits), so that one 128-bit shared
+//      load brings a stencil tap's three values and the flags its order test needs;
+//   4. every target: refined start, element walk with FP32 Newton inversion (Sec. 2.2, eq.
+//      mapping1), order from the OR of the 16 taps' flag bits, cubic and bilinear tensor sums
+//      (eq. multiZ) on packed FP32x2 FMAs.  Consecutive lanes take consecutive targets of a row,
+//      so that their shared-memory reads fall in distinct banks.
+// The window of the CTA's next tile is copied while the current tile is computed (two window
+// slots); the next tile's displacements are loaded into registers one tile ahead.  Targets the
+// fast path cannot finish (walk leaves the window, FP32 Newton fails or meets a nearly degenerate
+// element) take the general path of the shared tile body: walk with global reads, FP64 re-solve.
+//
+// Waits on an mbarrier are bounded in time; a wait that runs out is counted in the grid's
+// timeout counter and the CTA stops (the host reports SL_ERR_CUDA).
+#pragma once
+
+#include <cuda.h>
+
+#include "sl_tile2d.cuh"
+
+namespace {
+
+// TX x TY targets per tile, NT threads (each a column of both halves of the tile row per pass), window capacity
+// WX x WY nodes (WX a multiple of 4 for the TMA box, WY a multiple of the 8-row strip)
+template <int TX_, int TY_, int NT_, int WX_, int WY_, int MINB_>
+struct R2Cfg {
+    static constexpr int TX = TX_, TY = TY_, NT = NT_, WX = WX_, WY = WY_, MINB = MINB_;
+    static constexpr int PX = TX / 2;          // target pairs per tile row
+    static constexpr int ROWS = NT / PX;       // tile rows per pass
+    static constexpr int PPT = TY / ROWS;      // pairs per thread
+    static constexpr int STRIP = 8;            // rows per TMA box
+    static constexpr int CH = 4;               // rows per work item of the flag pass
+    static_assert(PX % 16 == 0 && NT % PX == 0 && TY % ROWS == 0, "bad remap2d tile");
+    static_assert(WX % 4 == 0 && WY % STRIP == 0 && 2 * WX <= 256, "bad remap2d window");
+    // dynamic shared memory (bytes): planar staging of 3 planes, two displacement windows, the
+    // float4 records, two slots of start points
+    static constexpr size_t STAGE = 3ull * WY * WX * 4, DWIN = 2ull * WY * WX * 8, REC = 1ull * WY * WX * 16;
+    static constexpr size_t SPTS = 2ull * (TX * TY) * 8;
+    static constexpr size_t SMEM = STAGE + DWIN + REC + SPTS + 128;  // + room to align the base
+};
+typedef R2Cfg<64, 32, 512, 88, 48, 1> R2Wide;    // one CTA of 16 warps per SM
+typedef R2Cfg<32, 32, 256, 44, 48, 2> R2Square;  // two CTAs of 8 warps per SM
+
+struct R2Maps {
+    CUtensorMap f[3];  // field planes: FP32, dims (n0, n1), box (WX, 8)
+    CUtensorMap D;     // displacement as FP32 pairs: dims (2 n0, n1), box (2 WX, 8)
+};
+
+// window of one tile: origin, extent, and how it is staged
+struct Win2 {
+    int lox, loy, wx, wy;
+    int mode;  // 0: not staged (general path), 1: TMA boxes, 2: per-element copies
+};
+
+template <int WX>
+__device__ __forceinline__ bool w2_has(const Win2 &w, int x, int y)
+{
+    return (unsigned)(x - w.lox) < (unsigned)w.wx && (unsigned)(y - w.loy) < (unsigned)w.wy;
+}
+template <int WX>
+__device__ __forceinline__ int w2_at(const Win2 &w, int x, int y)
+{
+    return (y - w.loy) * WX + (x - w.lox);
+}
+
+// ---- mbarrier and bulk-tensor copies (inline PTX) ---------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// this thread's earlier cp.async copies arrive on the barrier when they complete (the pending count
+// is raised first, so the phase still needs the barrier's own arrival)
+__device__ __forceinline__ void mbar_track_cp_async(unsigned long long *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of the barrier, giving up after 0.2 s (a copy that never lands).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_test(bar, parity)) return true;
+        if (global_ns() - t0 > 200000000ull) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+// order this thread's generic-proxy accesses of shared memory before later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct R2Args {
+    TileArgs t;        // grid, fields, displacement, counters (the shared tile body's arguments)
+    int tiles_x, ntiles;
+    int use_tma;       // the tensor maps are valid
+    unsigned long long *timeouts;  // counter of waits that ran out
+};
+
+// ---- window of a tile from the box of its start elements --------------------------------------
+template <class Cfg>
+__device__ __forceinline__ Win2 window2(int bx0, int by0, int bx1, int by1, int n0, int n1, bool tma)
+{
+    Win2 w;
+    // nodes x0 .. x1 the walk (slack 1), the stencil (c-1 .. c+2) and the limiter (one more on
+    // each side) may touch; the origin is rounded down to a multiple of 4 for the box copies
+    const long long x0 = (long long)bx0 - WALK_SLACK - 2, x1 = (long long)bx1 + WALK_SLACK + 3;
+    const long long y0 = (long long)by0 - WALK_SLACK - 2, y1 = (long long)by1 + WALK_SLACK + 3;
+    const long long lox = x0 & ~3LL;
+    const long long wx = x1 - lox + 1, wy = y1 - y0 + 1;
+    const bool fits = bx0 <= bx1 && by0 <= by1 && wx <= Cfg::WX && wy <= Cfg::WY && lox >= -n0 && y0 >= -n1 &&
+                      lox + wx <= 2LL * n0 && y0 + wy <= 2LL * n1;
+    w.lox = fits ? (int)lox : 0;
+    w.loy = fits ? (int)y0 : 0;
+    w.wx = fits ? (int)wx : 0;
+    w.wy = fits ? (int)wy : 0;
+    w.mode = !fits ? 0 : (tma && lox >= 0 && y0 >= 0 && lox + wx <= n0 && y0 + wy <= n1) ? 1 : 2;
+    return w;
+}
+
+// ---- Sec. 2.2 element search with global reads where the window ends (general path) ----------
+template <class Cfg, typename TN>
+__device__ __forceinline__ int walk2w(const TileArgs &a, const Win2 &w, const float2 *sD, int jx, int jy, int &cx,
+                                      int &cy, TN xi[3], int &hops, int &iters, bool &degen)
+{
+    const TN tol = sizeof(TN) == 8 ? TN(1e-14) : TN(SL_NEWTON_TOL_F32);
+    const TN slack = sizeof(TN) == 8 ? TN(1e-12) : TN(SL_SLACK_F32);
+    CycleCheck cyc;
+    cyc.start(cx, cy, 0);
+    for (int hop = 0; hop < a.walk_max; ++hop) {
+        TN P[8][3];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int x = cx + (v & 1), y = cy + (v >> 1);
+            const float2 d = (w.mode != 0 && w2_has<Cfg::WX>(w, x, y))
+                                 ? sD[w2_at<Cfg::WX>(w, x, y)]
+                                 : __ldg(reinterpret_cast<const float2 *>(a.D) + gidx(x, y, a.n0, a.n1));
+            P[v][0] = TN(x - jx) + TN(d.x);
+            P[v][1] = TN(y - jy) + TN(d.y);
+        }
+        int it = 0;
+        const int st = newton_solve2<TN>(P, a.max_iter, tol, xi, &it, &degen);
+        hops += 1;
+        iters += it;
+        if (!(finite_t(xi[0]) && finite_t(xi[1]))) return st == ST_OK ? ST_NEWTON : st;
+        const bool inside = xi[0] >= -slack && xi[0] <= TN(1) + slack && xi[1] >= -slack && xi[1] <= TN(1) + slack;
+        if (inside) return st;
+        if (xi[0] < -slack)
+            cx -= 1;
+        else if (xi[0] > TN(1) + slack)
+            cx += 1;
+        if (xi[1] < -slack)
+            cy -= 1;
+        else if (xi[1] > TN(1) + slack)
+            cy += 1;
+        if (cyc.step(cx, cy, 0)) return ST_LOCATE;
+    }
+    return ST_LOCATE;
+}
+
+// Start element of a target: one fixed-point step s <- j - D(s) from s0 = j - D_j with D(s0)
+// bilinear in the staged window (the walk still decides); floor(s0) when not staged.
+template <class Cfg>
+__device__ __forceinline__ void refined_start2(const Win2 &w, const float2 *sD, int jx, int jy, float sx, float sy,
+                                               int &ex, int &ey)
+{
+    ex = (int)floorf(sx);
+    ey = (int)floorf(sy);
+    if (w.mode == 0 || !(w2_has<Cfg::WX>(w, ex, ey) && w2_has<Cfg::WX>(w, ex + 1, ey + 1))) return;
+    const int i0 = w2_at<Cfg::WX>(w, ex, ey);
+    const float fx = sx - (float)ex, fy = sy - (float)ey;
+    const float2 d00 = sD[i0], d10 = sD[i0 + 1], d01 = sD[i0 + Cfg::WX], d11 = sD[i0 + Cfg::WX + 1];
+    const float bx = fmaf(fx, d10.x - d00.x, d00.x), by = fmaf(fx, d10.y - d00.y, d00.y);
+    const float dx = fmaf(fy, fmaf(fx, d11.x - d01.x, d01.x) - bx, bx);
+    const float dy = fmaf(fy, fmaf(fx, d11.y - d01.y, d01.y) - by, by);
+    const float rx = (float)jx - dx, ry = (float)jy - dy;
+    if (finite_t(rx) && finite_t(ry) && fabsf(rx - sx) < 4.f && fabsf(ry - sy) < 4.f) {
+        ex = (int)floorf(rx);
+        ey = (int)floorf(ry);
+    }
+}
+
+// Sec. 2.2 element search inside the staged window, FP32 Newton (the arithmetic of walk2w<float>).
+// False when the walk leaves the window, Newton fails or the element is nearly degenerate.
+template <class Cfg>
+__device__ __forceinline__ bool walk_fast2(const Win2 &w, const float2 *sD, int walk_max, int max_iter, int jx, int jy,
+                                           int &ex, int &ey, float &xi0, float &xi1, int &hops, int &iters)
+{
+    const float slack = SL_SLACK_F32;
+    CycleCheck cyc;
+    cyc.start(ex, ey, 0);
+    for (int hop = 0; hop < walk_max; ++hop) {
+        if (!(w2_has<Cfg::WX>(w, ex, ey) && w2_has<Cfg::WX>(w, ex + 1, ey + 1))) return false;
+        const int i0 = w2_at<Cfg::WX>(w, ex, ey);
+        const float2 d0 = sD[i0], d1 = sD[i0 + 1], d2 = sD[i0 + Cfg::WX], d3 = sD[i0 + Cfg::WX + 1];
+        const float rx0 = (float)(ex - jx), rx1 = (float)(ex + 1 - jx);
+        const float ry0 = (float)(ey - jy), ry1 = (float)(ey + 1 - jy);
+        float P[8][3];
+        P[0][0] = rx0 + d0.x;
+        P[0][1] = ry0 + d0.y;
+        P[1][0] = rx1 + d1.x;
+        P[1][1] = ry0 + d1.y;
+        P[2][0] = rx0 + d2.x;
+        P[2][1] = ry1 + d2.y;
+        P[3][0] = rx1 + d3.x;
+        P[3][1] = ry1 + d3.y;
+        float xf[3];
+        int it = 0;
+        bool degen = false;
+        const int st = newton_solve2<float>(P, max_iter, SL_NEWTON_TOL_F32, xf, &it, &degen);
+        hops += 1;
+        iters += it;
+        if (st != ST_OK || degen) return false;
+        const bool lo0 = xf[0] < -slack, hi0 = xf[0] > 1.f + slack;
+        const bool lo1 = xf[1] < -slack, hi1 = xf[1] > 1.f + slack;
+        if (!(lo0 || hi0 || lo1 || hi1)) {
+            xi0 = xf[0];
+            xi1 = xf[1];
+            return true;
+        }
+        ex += lo0 ? -1 : (hi0 ? 1 : 0);
+        ey += lo1 ? -1 : (hi1 ? 1 : 0);
+        if (cyc.step(ex, ey, 0)) return false;
+    }
+    return false;
+}
+
+// eq. (multiZ) from the float4 records of the 4x4 stencil starting at r (pitch WX): the cubic sum
+// of fields 0, 1 (packed pair) and 2 (the pair with the flag word, whose second lane is unused),
+// the bilinear sum over the element's own vertices, and the OR of the 16 flag words.  Fields whose
+// flag bit is set anywhere in the stencil take the bilinear value (Sec. 2.3; order 0 for every
+// field when max_order is 0).
+template <int WX, int NF>
+__device__ __forceinline__ void stencil_sum(const float4 *r, float xi0, float xi1, bool limit, bool linear_only,
+                                            float v[3], unsigned &nlin)
+{
+    float wc[2][4];
+    cubic_weights(xi0, wc[0]);
+    cubic_weights(xi1, wc[1]);
+    const float2 w0 = bcast2(wc[0][0]), w1 = bcast2(wc[0][1]), w2 = bcast2(wc[0][2]), w3 = bcast2(wc[0][3]);
+    const float2 u0 = bcast2(1.f - xi0), u1 = bcast2(xi0);
+    const float2 z = make_float2(0.f, 0.f);
+    float2 cl = z, ch = z, ll = z, lh = z;
+    unsigned bits = 0u;
+#pragma unroll
+    for (int ky = 0; ky < 4; ++ky) {
+        const float4 t0 = r[0], t1 = r[1], t2 = r[2], t3 = r[3];
+        bits |= __float_as_uint(t0.w) | __float_as_uint(t1.w) | __float_as_uint(t2.w) | __float_as_uint(t3.w);
+        const float2 wy = bcast2(wc[1][ky]);
+        float2 q = __fmul2_rn(w0, lo2(t0));
+        q = __ffma2_rn(w1, lo2(t1), q);
+        q = __ffma2_rn(w2, lo2(t2), q);
+        q = __ffma2_rn(w3, lo2(t3), q);
+        cl = __ffma2_rn(wy, q, cl);
+        if (NF > 2) {
+            float2 p = __fmul2_rn(w0, hi2(t0));
+            p = __ffma2_rn(w1, hi2(t1), p);
+            p = __ffma2_rn(w2, hi2(t2), p);
+            p = __ffma2_rn(w3, hi2(t3), p);
+            ch = __ffma2_rn(wy, p, ch);
+        }
+        if (ky == 1 || ky == 2) {
+            const float2 vy = bcast2(ky == 1 ? 1.f - xi1 : xi1);
+            ll = __ffma2_rn(vy, __ffma2_rn(u1, lo2(t2), __fmul2_rn(u0, lo2(t1))), ll);
+            if (NF > 2) lh = __ffma2_rn(vy, __ffma2_rn(u1, hi2(t2), __fmul2_rn(u0, hi2(t1))), lh);
+        }
+        r += WX;
+    }
+    const unsigned lin = linear_only ? 7u : (limit ? bits : 0u);
+    v[0] = (lin & 1u) ? ll.x : cl.x;
+    v[1] = (lin & 2u) ? ll.y : cl.y;
+    v[2] = (lin & 4u) ? lh.x : ch.x;
+    nlin = __popc(lin & ((1u << NF) - 1u));
+}
+
+// The general path of one target (rare, out of line): walk from the refined start with global
+// reads where the window ends; on failure or a nearly degenerate element the FP64 re-solve from the
+// first start element; then order and sum from the records when the stencil lies in the flagged
+// part of the window, from global memory otherwise.  A target that still fails keeps its values.
+template <class Cfg, int NF>
+__device__ __noinline__ TargetOut slow_target2(const TileArgs &a, const Win2 w, const float2 *sD, const float4 *sR,
+                                               bool limit, int jx, int jy, int ex, int ey, int c0x, int c0y)
+{
+    TargetOut r = {ST_OK, 0, 0, 0, 0};
+    const long long jj = (long long)jy * a.n0 + jx;
+    float xf[3] = {0.f, 0.f, 0.f};
+    bool degen = false;
+    int st = walk2w<Cfg, float>(a, w, sD, jx, jy, ex, ey, xf, r.hops, r.iters, degen);
+    float xi0 = xf[0], xi1 = xf[1];
+    if (st != ST_OK || degen) {
+        if (st == ST_LOCATE || st == ST_FOLD) {
+            ex = c0x;
+            ey = c0y;
+        }
+        double xd[3] = {0.0, 0.0, 0.0};
+        bool dg = false;
+        st = walk2w<Cfg, double>(a, w, sD, jx, jy, ex, ey, xd, r.hops, r.iters, dg);
+        xi0 = (float)xd[0];
+        xi1 = (float)xd[1];
+        r.f64 = 1;
+    }
+    r.st = st;
+    if (st != ST_OK) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a.out[f][jj] = __ldg(a.in[f] + jj);
+        return r;
+    }
+    const int rx = ex - w.lox, ry = ey - w.loy;
+    const bool fast = w.mode != 0 && rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;
+    if (fast) {
+        float v[3];
+        unsigned nlin;
+        stencil_sum<Cfg::WX, NF>(sR + (ry - 1) * Cfg::WX + (rx - 1), xi0, xi1, limit, a.max_order == 0, v, nlin);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a.out[f][jj] = v[f];
+        r.nlin = (int)nlin;
+    } else {
+        const unsigned lin_mask = a.max_order == 0 ? 0xffu : (limit ? box_flags_global(a, ex, ey) : 0u);
+        r.nlin = __popc(lin_mask & ((1u << NF) - 1u));
+        interp_global(a, jj, ex, ey, xi0, xi1, lin_mask);
+    }
+    return r;
+}
+
+// ---- the flag pass: planar staging -> float4 records with the flag bits -------------------------
+// Records are written for the window's interior nodes (1 .. wx-2, 1 .. wy-2), whose four
+// neighbours are staged.  A work item is one column over CH rows (consecutive threads take
+// consecutive columns); it keeps the column's values of the previous and current rows in
+// registers and reads the row neighbours and the next row from the staging planes.
+template <class Cfg, int NF>
+__device__ __forceinline__ void flag_pass(const Win2 &w, const float *stage, float4 *sR, float thr, bool limit)
+{
+    constexpr int WX = Cfg::WX, CH = Cfg::CH, PLANE = WX * Cfg::WY;
+    const int ncol = w.wx - 2;
+    const int nch = (w.wy - 2 + CH - 1) / CH;
+    const int items = ncol * nch;
+    for (int q = threadIdx.x; q < items; q += Cfg::NT) {
+        const int ch = q / ncol, x = 1 + (q - ch * ncol);
+        const int y0 = 1 + ch * CH, y1 = min(y0 + CH, w.wy - 1);
+        float up[NF], c[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float *p = stage + f * PLANE + (y0 - 1) * WX + x;
+            up[f] = p[0];
+            c[f] = p[WX];
+        }
+        for (int y = y0; y < y1; ++y) {
+            unsigned bits = 0u;
+            float vals[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const float *p = stage + f * PLANE + y * WX + x;
+                const float l = p[-1], r = p[1], dn = p[WX];
+                // Sec. 2.3 along y and along x: flagged where |dp - dm| > thr max(|dp|, |dm|)
+                if (limit && (jump_test<float>(up[f], c[f], dn, thr) || jump_test<float>(l, c[f], r, thr)))
+                    bits |= 1u << f;
+                vals[f] = c[f];
+                up[f] = c[f];
+                c[f] = dn;
+            }
+            sR[y * WX + x] = make_float4(vals[0], vals[1], vals[2], __uint_as_float(bits));
+        }
+    }
+}
+
+// ---- staging of one window --------------------------------------------------------------------
+// TMA: thread 0 arms the barrier with the bytes of every strip and issues the box copies.
+// Per-element copies: every thread copies its share and makes the barrier track its copies; thread
+// 0 adds the barrier's own arrival after a CTA barrier (mbar_finish).  Not staged: thread 0 arrives.
+template <class Cfg, int NF>
+__device__ __forceinline__ void stage_window2(const R2Args &A, const R2Maps &maps, const Win2 &w, float *stage,
+                                              float2 *sD, unsigned long long *bar)
+{
+    constexpr int WX = Cfg::WX, PLANE = WX * Cfg::WY, S = Cfg::STRIP;
+    if (w.mode == 1) {
+        if (threadIdx.x == 0) {
+            const int ns = (w.wy + S - 1) / S;
+            mbar_arrive_tx(bar, (unsigned)(ns * S * WX * 4 * (NF + 2)));
+            for (int s = 0; s < ns; ++s) {
+                const int y = w.loy + s * S;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * PLANE + s * S * WX, &maps.f[f], w.lox, y, bar);
+                tma_load_2d(sD + s * S * WX, &maps.D, 2 * w.lox, y, bar);
+            }
+        }
+    } else if (w.mode == 2) {
+        const TileArgs &a = A.t;
+        const int nwin = w.wx * w.wy;
+        const float inv_wx = 1.f / (float)w.wx;
+        for (int q = threadIdx.x; q < nwin; q += Cfg::NT) {
+            const int yy = row_of(q, inv_wx), xx = q - yy * w.wx;
+            const long long gi = (long long)wrap_near(w.loy + yy, a.n1) * a.n0 + wrap_near(w.lox + xx, a.n0);
+            const int o = yy * WX + xx;
+            cp_async<8>(sD + o, reinterpret_cast<const float2 *>(a.D) + gi);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) cp_async<4>(stage + f * PLANE + o, a.in[f] + gi);
+        }
+        mbar_track_cp_async(bar);
+    }
+}
+// the barrier's own arrival for windows not armed by the TMA path; after a CTA barrier that
+// follows every thread's mbar_track_cp_async
+__device__ __forceinline__ void mbar_finish(const Win2 &w, unsigned long long *bar)
+{
+    if (threadIdx.x == 0 && w.mode != 1) mbar_arrive(bar);
+}
+
+// Targets of a thread: column px of each half of the tile row (x0 + px and x0 + px + TX/2, so that
+// consecutive lanes read consecutive shared-memory records), rows py + k ROWS.
+template <class Cfg>
+__device__ __forceinline__ int target_x(int x0, int h) { return x0 + (int)(threadIdx.x % Cfg::PX) + h * Cfg::PX; }
+template <class Cfg>
+__device__ __forceinline__ int target_y(int y0, int k) { return y0 + (int)(threadIdx.x / Cfg::PX) + k * Cfg::ROWS; }
+
+// start points of tile t's targets from the displacements in registers, into slot S (float2 per
+// target, index (2 k + h) NT + thread); their box
+template <class Cfg>
+__device__ __forceinline__ void start_points2(const TileArgs &a, int x0, int y0, const float2 *dj, float2 *S, int &mnx,
+                                              int &mny, int &mxx, int &mxy)
+{
+    mnx = mny = INT_MAX;
+    mxx = mxy = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < Cfg::PPT; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jx = target_x<Cfg>(x0, h), jy = target_y<Cfg>(y0, k);
+            float2 s = make_float2((float)jx, (float)jy);
+            if (jx < a.n0 && jy < a.n1) {
+                s = start_point(jx, jy, dj[2 * k + h]);
+                mnx = min(mnx, (int)floorf(s.x));
+                mny = min(mny, (int)floorf(s.y));
+                mxx = max(mxx, (int)floorf(s.x));
+                mxy = max(mxy, (int)floorf(s.y));
+            }
+            S[(2 * k + h) * Cfg::NT + threadIdx.x] = s;
+        }
+    }
+}
+
+// displacements of tile t's targets into registers
+template <class Cfg>
+__device__ __forceinline__ void load_dj(const TileArgs &a, int x0, int y0, float2 *dj)
+{
+#pragma unroll
+    for (int k = 0; k < Cfg::PPT; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jx = target_x<Cfg>(x0, h), jy = target_y<Cfg>(y0, k);
+            dj[2 * k + h] = (jx < a.n0 && jy < a.n1)
+                                ? __ldg(reinterpret_cast<const float2 *>(a.D) + ((long long)jy * a.n0 + jx))
+                                : make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// box reduction of the CTA's start elements into the window of slot p (thread 0 writes it and
+// resets the box); a CTA barrier inside
+template <class Cfg>
+__device__ __forceinline__ void reduce_window(const R2Args &A, int mnx, int mny, int mxx, int mxy, int *box, Win2 *W,
+                                              int p)
+{
+    mnx = __reduce_min_sync(0xffffffffu, mnx);
+    mny = __reduce_min_sync(0xffffffffu, mny);
+    mxx = __reduce_max_sync(0xffffffffu, mxx);
+    mxy = __reduce_max_sync(0xffffffffu, mxy);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&box[0], mnx);
+        atomicMin(&box[1], mny);
+        atomicMax(&box[2], mxx);
+        atomicMax(&box[3], mxy);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        W[p] = window2<Cfg>(box[0], box[1], box[2], box[3], A.t.n0, A.t.n1, A.use_tma != 0);
+        box[0] = box[1] = INT_MAX;
+        box[2] = box[3] = INT_MIN;
+    }
+}
+
+// Phase 4 of one tile: every target of the thread; general-path targets after the loop.
+template <class Cfg, int NF>
+__device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0, const Win2 &w, const float2 *sD,
+                                              const float4 *sR, const float2 *S, LocalCounters &cnt)
+{
+    constexpr int WX = Cfg::WX;
+    const bool limit = a.max_order >= 1 && a.thr >= 0.f;
+    const bool lin_only = a.max_order == 0;
+    if (w.mode == 0 && threadIdx.x == 0) cnt.fallback += 1;
+    unsigned slow = 0u;
+#pragma unroll 1
+    for (int q = 0; q < 2 * Cfg::PPT; ++q) {
+        const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
+        if (jx >= a.n0 || jy >= a.n1) continue;
+        const float2 s = S[q * Cfg::NT + threadIdx.x];
+        int ex, ey;
+        refined_start2<Cfg>(w, sD, jx, jy, s.x, s.y, ex, ey);
+        int hops = 0, iters = 0;
+        float xi0 = 0.f, xi1 = 0.f;
+        bool good = w.mode != 0 && walk_fast2<Cfg>(w, sD, a.walk_max, a.max_iter, jx, jy, ex, ey, xi0, xi1, hops, iters);
+        const int rx = ex - w.lox, ry = ey - w.loy;
+        good = good && rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;
+        if (good) {
+            float v[3];
+            unsigned nlin;
+            stencil_sum<WX, NF>(sR + (ry - 1) * WX + (rx - 1), xi0, xi1, limit, lin_only, v, nlin);
+            const long long jj = (long long)jy * a.n0 + jx;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a.out[f][jj] = v[f];
+            cnt.targets += 1;
+            cnt.hops += hops;
+            cnt.hops_max = max(cnt.hops_max, (unsigned)hops);
+            cnt.iters += iters;
+            cnt.iters_max = max(cnt.iters_max, (unsigned)iters);
+            cnt.oh0 += nlin;
+            cnt.oh1 += NF - nlin;
+        } else {
+            slow |= 1u << q;
+        }
+    }
+#pragma unroll 1
+    for (int q = 0; slow != 0u; ++q, slow >>= 1) {
+        if (!(slow & 1u)) continue;
+        const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
+        const float2 s = S[q * Cfg::NT + threadIdx.x];
+        int ex, ey;
+        refined_start2<Cfg>(w, sD, jx, jy, s.x, s.y, ex, ey);
+        const TargetOut r = slow_target2<Cfg, NF>(a, w, sD, sR, limit, jx, jy, ex, ey, (int)floorf(s.x), (int)floorf(s.y));
+        cnt.targets += 1;
+        cnt.hops += r.hops;
+        cnt.hops_max = max(cnt.hops_max, (unsigned)r.hops);
+        cnt.iters += r.iters;
+        cnt.iters_max = max(cnt.iters_max, (unsigned)r.iters);
+        cnt.f64 += r.f64;
+        if (r.st != ST_OK) {
+            cnt.fl += r.st == ST_LOCATE;
+            cnt.fn += r.st == ST_NEWTON;
+            cnt.ff += r.st == ST_FOLD;
+        } else {
+            cnt.oh0 += r.nlin;
+            cnt.oh1 += NF - r.nlin;
+        }
+    }
+}
+
+// eq. (vel): the next step's trajectories of the tile's own nodes (fused steps; the velocity is
+// given, so they do not depend on the fields being remapped)
+template <class Cfg>
+__device__ __forceinline__ void integrate_next2(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0)
+{
+#pragma unroll 1
+    for (int q = 0; q < 2 * Cfg::PPT; ++q) {
+        const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
+        if (jx >= a.n0 || jy >= a.n1) continue;
+        float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
+        trajectory_cells<float, 2>(vn, X, d);
+        reinterpret_cast<float2 *>(a.D_next)[(long long)jy * a.n0 + jx] = make_float2(d[0], d[1]);
+    }
+}
+
+template <class Cfg, int NF, bool FUSED>
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
+    remap2d_tma_kernel(const __grid_constant__ R2Args A, const __grid_constant__ R2Maps maps, const VelArgs<float> vn)
+{
+    constexpr int WX = Cfg::WX, WY = Cfg::WY, TX = Cfg::TX, TY = Cfg::TY, PPT = Cfg::PPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // box copies want 128-byte aligned destinations: the launch adds 128 bytes of room
+    unsigned char *const smem =
+        smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    float *const stage = reinterpret_cast<float *>(smem);
+    float2 *const dwin = reinterpret_cast<float2 *>(smem + Cfg::STAGE);
+    float4 *const rec = reinterpret_cast<float4 *>(smem + Cfg::STAGE + Cfg::DWIN);
+    float2 *const spts = reinterpret_cast<float2 *>(smem + Cfg::STAGE + Cfg::DWIN + Cfg::REC);
+    __shared__ unsigned long long bar[2];
+    __shared__ int box[4];
+    __shared__ Win2 W[2];
+    __shared__ int abort_flag;
+    const TileArgs &a = A.t;
+    const int G = (int)gridDim.x;
+    LocalCounters cnt;
+    cnt.clear();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        box[0] = box[1] = INT_MAX;
+        box[2] = box[3] = INT_MIN;
+        abort_flag = 0;
+    }
+    __syncthreads();
+    unsigned phase = 0u;  // bit p: parity of slot p's next phase
+    int t = blockIdx.x;
+    float2 dj[2 * PPT];
+    if (t < A.ntiles) {
+        // prologue: start points and window of the first tile, displacements of the second
+        const int tr = t / A.tiles_x;
+        load_dj<Cfg>(a, (t - tr * A.tiles_x) * TX, tr * TY, dj);
+        int mnx, mny, mxx, mxy;
+        start_points2<Cfg>(a, (t - tr * A.tiles_x) * TX, tr * TY, dj, spts, mnx, mny, mxx, mxy);
+        reduce_window<Cfg>(A, mnx, mny, mxx, mxy, box, W, 0);
+        __syncthreads();
+        stage_window2<Cfg, NF>(A, maps, W[0], stage, dwin, &bar[0]);
+        __syncthreads();
+        mbar_finish(W[0], &bar[0]);
+        if (t + G < A.ntiles) {
+            const int t2 = t + G, tr2 = t2 / A.tiles_x;
+            load_dj<Cfg>(a, (t2 - tr2 * A.tiles_x) * TX, tr2 * TY, dj);
+        }
+    }
+    for (int k = 0; t < A.ntiles; ++k, t += G) {
+        const int p = k & 1;
+        const int tr = t / A.tiles_x, x0 = (t - tr * A.tiles_x) * TX, y0 = tr * TY;
+        const int tn = t + G;
+        // start points and window of the next tile (its displacements are in registers)
+        if (tn < A.ntiles) {
+            const int trn = tn / A.tiles_x;
+            int mnx, mny, mxx, mxy;
+            start_points2<Cfg>(a, (tn - trn * A.tiles_x) * TX, trn * TY, dj, spts + (p ^ 1) * 2 * PPT * Cfg::NT, mnx, mny,
+                               mxx, mxy);
+            reduce_window<Cfg>(A, mnx, mny, mxx, mxy, box, W, p ^ 1);
+            if (tn + G < A.ntiles) {
+                const int t2 = tn + G, tr2 = t2 / A.tiles_x;
+                load_dj<Cfg>(a, (t2 - tr2 * A.tiles_x) * TX, tr2 * TY, dj);
+            }
+        }
+        // this tile's window
+        if (threadIdx.x == 0 && !mbar_wait(&bar[p], (phase >> p) & 1u)) {
+            atomicAdd(A.timeouts, 1ull);
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        // the phase has completed: every thread observes it once, which orders the copies' data
+        // before its own reads
+        (void)mbar_test(&bar[p], (phase >> p) & 1u);
+        phase ^= 1u << p;
+        const Win2 w = W[p];
+        if (w.mode != 0) flag_pass<Cfg, NF>(w, stage, rec, a.thr, a.max_order >= 1 && a.thr >= 0.f);
+        fence_proxy_async();  // the staging planes' reads before the next box copies overwrite them
+        __syncthreads();
+        // the staging planes are free: copy the next tile's window while this one is computed
+        if (tn < A.ntiles) {
+            stage_window2<Cfg, NF>(A, maps, W[p ^ 1], stage, dwin + (p ^ 1) * WX * WY, &bar[p ^ 1]);
+        }
+        if (FUSED && a.D_next != nullptr) integrate_next2<Cfg>(a, vn, x0, y0);
+        compute_tile2<Cfg, NF>(a, x0, y0, w, dwin + p * WX * WY, rec, spts + p * 2 * PPT * Cfg::NT, cnt);
+        __syncthreads();
+        if (tn < A.ntiles) mbar_finish(W[p ^ 1], &bar[p ^ 1]);
+    }
+    flush_counters(cnt, a.counters);
+}
+
+}  // namespace

@@ -1,6 +1,8 @@
-// sl_tiled.cu -- dispatch of the FP32 production kernels: 2-D grids go to the shared-memory tiled
-// kernels (sl_tile2d.cuh, one translation unit per tile configuration; the quintic Z-spline to
-// sl_tiled_z2.cu), 3-D grids to the blocked kernels (sl_blocked3d.cu, cubic and linear only).
+// sl_tiled.cu -- dispatch of the FP32 production kernels: 2-D grids go to the persistent kernel with
+// TMA-staged windows (sl_remap2d.cuh; tile configurations 0, 6, 7, up to 3 fields, analytic
+// velocities) or to the shared-memory tiled kernels (sl_tile2d.cuh, one translation unit per tile
+// configuration; the quintic Z-spline to sl_tiled_z2.cu), 3-D grids to the blocked kernels
+// (sl_blocked3d.cu, cubic and linear only).
 #include <string.h>
 
 #include "sl_internal.h"
@@ -26,7 +28,10 @@ static cudaError_t launch_tiled2d(const sl_grid *g, const void *D, void *D_next,
                                   const void *const *in, void *const *out, cudaStream_t s)
 {
     if (g->desc.max_order > 1) return launch_tiled2d_z2(g, D, D_next, t_next, dt, fused, in, out, s);
-    switch (g->desc.tile_config) {
+    const int c = g->desc.tile_config;
+    if ((c == 0 || c == 6 || c == 7) && remap2d_tma_supported(g, in, out))
+        return launch_remap2d_tma(g, c == 6 ? 6 : 7, D, D_next, t_next, dt, fused, in, out, s);
+    switch (c) {
     case 5:
         if (g->nfields <= 4) return launch_tiled2d_cfgp(g, D, D_next, t_next, dt, fused, in, out, s);
         return launch_tiled2d_cfga(g, D, D_next, t_next, dt, fused, in, out, s);

@@ -55,7 +55,7 @@ class sl_diag(C.Structure):
     _fields_ = [(name, C.c_uint64) for name in (
         "targets", "fail_locate", "fail_newton", "fail_fold", "hops_sum", "hops_max", "iters_sum", "iters_max",
         "newton_f64")] + [("order_hist", C.c_uint64 * 3), ("tiles_fallback", C.c_uint64),
-                    ("kernel_launches", C.c_uint64)]
+                    ("kernel_launches", C.c_uint64), ("timeouts", C.c_uint64)]
 
     def as_dict(self):
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "order_hist"}
@@ -92,6 +92,7 @@ def lib():
             "sl_remap_fields": (C.c_int, [vp, pp, pp, vp]),
             "sl_remap_fields_debug": (C.c_int, [vp, pp, pp, C.POINTER(sl_remap_debug), vp]),
             "sl_step": (C.c_int, [vp, pp, pp, C.c_double, C.c_double, C.c_int, vp]),
+            "sl_step_out": (C.c_int, [vp, pp, pp, pp, C.c_double, C.c_double, C.c_int, vp]),
             "sl_moments": (C.c_int, [vp, vp, C.c_int, dp, vp]),
             "sl_compute_flags": (C.c_int, [vp, pp, vp, vp]),
             "sl_set_displacement": (C.c_int, [vp, vp, i64, vp]),
@@ -227,6 +228,13 @@ def sl_step(h, fields, scratch, t0: float, dt: float, nsteps: int, stream=None):
     _check(lib().sl_step(h, pf, ps, float(t0), float(dt), int(nsteps), _stream(stream)), "sl_step")
 
 
+def sl_step_out(h, fin, fout, scratch, t0: float, dt: float, nsteps: int, stream=None):
+    pi, _a = _planes(fin)
+    po, _b = _planes(fout)
+    ps, _c = _planes(scratch) if scratch is not None else (None, None)
+    _check(lib().sl_step_out(h, pi, po, ps, float(t0), float(dt), int(nsteps), _stream(stream)), "sl_step_out")
+
+
 def sl_moments(h, field: torch.Tensor, pmax: int = 4, stream=None):
     out = (C.c_double * (pmax + 1))()
     _check(lib().sl_moments(h, C.c_void_p(field.data_ptr()), int(pmax), out, _stream(stream)), "sl_moments")
@@ -341,6 +349,12 @@ class Grid:
         """nsteps full steps from t0, in place on `fields` (`scratch`: the other half of the
         ping-pong pair, same shape)."""
         sl_step(self.handle, self._fit(fields), self._fit(scratch), t0, dt, nsteps, stream)
+
+    def step_out(self, fin: torch.Tensor, fout: torch.Tensor, t0, dt, nsteps, scratch=None, stream=None):
+        """nsteps full steps from t0 of `fin` (read only) into `fout`; `scratch` (same shape) is
+        needed for nsteps > 1."""
+        sl_step_out(self.handle, self._fit(fin), self._fit(fout), None if scratch is None else self._fit(scratch),
+                    t0, dt, nsteps, stream)
 
     def moments(self, field: torch.Tensor, pmax=4, stream=None):
         return sl_moments(self.handle, field, pmax, stream)
