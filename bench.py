@@ -4,8 +4,9 @@ Workload: the 2-D 1024^2 periodic swirling-deformation flow (T = 5) carrying thr
 (Gaussian sigma 0.1, a step with a circular jump of radius 0.2, sin(2pi x) sin(2pi y)), 4x4 cubic
 Z-spline stencil with limiter-driven order reduction, RK4 trajectories, dt = 5 dx (CFL 5).
 One benchmark step = one full FSL step (jump flags, RK4 trajectories, element search, Newton
-inversion, order selection, tensor Z-spline sum, reset) through sl_step on the FP32 production
-path (FP32 bulk, FP32 Newton with FP64 re-solves of near-degenerate targets).  L2 is flushed
+inversion, order selection, tensor Z-spline sum, reset) through sl_step_out on the FP32 production
+path (FP32 bulk, FP32 Newton with FP64 re-solves of near-degenerate targets): one launch per step,
+the input and result planes swapping roles each step; sl_step in place is reported beside it.  L2 is flushed
 (a 512 MiB write) before every timed step, so each step starts cold.
 
 Metric: node-updates/s (one node-update = one grid node advanced one full step, all 3 fields).
@@ -300,14 +301,20 @@ def kernel_only(args):
     return 0
 
 
-def batched_leg(torch, sl, inputs, steps=50, tile_config=0, max_order=1):
+def batched_leg(torch, sl, inputs, steps=50, tile_config=None, max_order=1):
     """512 independent 2-D grids (sides log-uniform in [32, 512], random Fourier streamfunctions,
-    Gaussian + step fields, FP32), all advanced 50 steps by one persistent launch per step under a
-    CUDA graph (cubic, or the quintic with max_order 2).  The working set (~0.8 GB) is larger than
-    L2."""
+    Gaussian + step fields, FP32; dt = 4 dx / the largest nodal speed), all advanced 50 steps by one
+    persistent launch per step under a CUDA graph (cubic, or the quintic with max_order 2).  The
+    working set (~0.8 GB) is larger than L2.  The tile configuration is the autotuner's pick, made
+    on the first 96 grids of the batch (two-step trials) unless one is given."""
+    from paper_1410_2817_gb300 import autotune
     wls = inputs.batched_grids(count=512, seed=0, steps=steps)
     for wl in wls:
         wl.max_order = max_order
+    tune = None
+    if tile_config is None:
+        tune = autotune.tune_batch(wls[:96], steps_per_trial=2, repeats=3)
+        tile_config = tune["best"]
     nodes = sum(wl.nnodes for wl in wls)
     grids = [sl.grid_for(wl, sl.SL_F32, tile_config=tile_config) for wl in wls]
     fields = [torch.tensor(wl.fields, dtype=torch.float32, device="cuda") for wl in wls]
@@ -328,7 +335,8 @@ def batched_leg(torch, sl, inputs, steps=50, tile_config=0, max_order=1):
                 for g in grids)
     out = {"workload": f"512 grids, sides 32-512 (seed 0), 2 fields, 50 steps, one graph replay, max_order {max_order}",
            "nodes": nodes, "value": nodes * steps / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
-           "launches_per_call": b.info()["launches"] - l0, "tile_config": tile_config, "failed_targets": fails}
+           "launches_per_call": b.info()["launches"] - l0, "tile_config": tile_config, "failed_targets": fails,
+           "autotune": tune}
     b.close()
     return out
 
@@ -367,6 +375,35 @@ def deform3d_leg(torch, sl, inputs, steps=5):
         tot = sum(a.elapsed_time(b) for a, b in ms)
         out[name] = {"workload": f"deform3d 256^3, 2 fields, FP32, max_order {mo}",
                      "value": wl.nnodes * nsteps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / nsteps}
+        if mo == 1:
+            # sl_remap_fields alone (box flags: two passes; the blocked remap), L2 flushed
+            g.advect(t, wl.dt)
+            o = torch.empty_like(f)
+            rm = []
+            for k in range(nsteps):
+                flush.fill_(k)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                g.remap(f, o)
+                b.record()
+                rm.append((a, b))
+            torch.cuda.synchronize()
+            remap_ms = sum(a.elapsed_time(b) for a, b in rm) / nsteps
+            hbm, kind = _peaks()
+            F, N3 = wl.nfields, wl.nnodes
+            step_bytes, remap_bytes = N3 * 2 * F * 4, N3 * (3 * 4 + 2 * F * 4)
+            sa = step_bytes / (tot / nsteps * 1e-3) / 1e9
+            ra = remap_bytes / (remap_ms * 1e-3) / 1e9
+            out[name]["roofline"] = {"bound": "hbm", "kernel": "the 3-D step: flags and x-OR, y/z-OR, blocked remap with "
+                                     "the next trajectories (three launches)", "achieved": sa, "peak": hbm,
+                                     "unit": "GB/s", "frac": sa / hbm, "traffic": None, "peak_kind": kind,
+                                     "algorithmic_bytes_per_launch": step_bytes,
+                                     "bytes_rule": "2 F T per node (16 B)", "timed_over": "the leg's flushed steps"}
+            out[name]["roofline_remap"] = {"bound": "hbm", "kernel": "sl_remap_fields 3-D (three launches)",
+                                           "achieved": ra, "peak": hbm, "unit": "GB/s", "frac": ra / hbm,
+                                           "traffic": None, "peak_kind": kind,
+                                           "algorithmic_bytes_per_launch": remap_bytes,
+                                           "bytes_rule": "d T + 2 F T per node (28 B)", "launch_ms": remap_ms}
         g.close()
     res = dict(out["cubic"])
     res["quintic_plain"] = out["quintic_plain"]
@@ -600,7 +637,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, 3-D and serving legs")
-    ap.add_argument("--serve-jobs", type=int, default=300, help="jobs of the served trace (0: skip)")
+    ap.add_argument("--serve-jobs", type=int, default=2000, help="jobs of the served trace (0: skip)")
     ap.add_argument("--mode", default="full", choices=["full", "remap", "step", "remap3d", "remap_z2", "nlsw"],
                     help="remap/step: only launch that call --steps times (for profilers); prints its timing")
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
@@ -626,19 +663,30 @@ def main():
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def run_path(dtype, newton, steps, warmup):
+    def run_path(dtype, newton, steps, warmup, in_place=False):
+        """One full step per call, L2 flushed before each: out of place through sl_step_out (the
+        planes of the step's input and result swap roles every step), or in place through sl_step
+        (whose one-step call copies its result back from the scratch planes)."""
         g = sl.grid_for(wl, dtype, newton_mode=newton)
         td = torch.float32 if dtype == sl.SL_F32 else torch.float64
         f = torch.tensor(wl.fields, dtype=td, device=dev)
         s = torch.empty_like(f)
         t = 0.0
+        bufs = [f, s]
+
+        def one(k, t):
+            if in_place:
+                g.step(f, s, t, wl.dt, 1)
+            else:
+                g.step_out(bufs[k & 1], bufs[(k + 1) & 1], t, wl.dt, 1)
+
         # the warm-up steps repeat the timed iteration exactly (L2 flush, events, one-step call):
         # the first flushed iterations after idle run ~1.5x slower (measured) and must not be timed
         for k in range(warmup):
             flush.fill_(k & 0xff)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            g.step(f, s, t, wl.dt, 1)
+            one(k, t)
             b.record(stream)
             t += wl.dt
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -648,13 +696,14 @@ def main():
         for k in range(steps):
             flush.fill_(k & 0xff)
             ev[k][0].record(stream)
-            g.step(f, s, t, wl.dt, 1)
+            one(warmup + k, t)
             ev[k][1].record(stream)
             t += wl.dt
         _barrier(dist, torch)
         wall = time.perf_counter() - w0
         ms = [a.elapsed_time(b) for a, b in ev]
-        return g, f, s, ms, wall, t, g.diagnostics()["kernel_launches"] - l0
+        cur = f if in_place or (warmup + steps) % 2 == 0 else s
+        return g, cur, (s if cur is f else f), ms, wall, t, g.diagnostics()["kernel_launches"] - l0
 
     # ---- FP32 production path (headline) -----------------------------------------------------
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -723,6 +772,14 @@ def main():
                  "launches": wl.steps + 1}
     gm.close()
 
+    # ---- the same steps in place through sl_step (one-step calls copy the result back) -------
+    gi, _, _, msi, _, _, launches_i = run_path(sl.SL_F32, sl.SL_NEWTON_MIXED, max(6, args.steps // 3), 3,
+                                              in_place=True)
+    gi.close()
+    in_place = {"value": ws * N * len(msi) / (_max_over_ranks(dist, torch, sum(msi)) * 1e-3), "unit": UNIT,
+                "ms_per_step": sum(msi) / len(msi), "launches_per_step": launches_i / len(msi),
+                "call": "sl_step(fields, scratch, t, dt, 1): the fused launch and the copy back of the result"}
+
     # ---- plain FP64 GPU path ----------------------------------------------------------------
     _, _, _, ms64, _, _, _ = run_path(sl.SL_F64, sl.SL_NEWTON_F64, args.fp64_steps, 3)
     fp64_value = ws * N * args.fp64_steps / (_max_over_ranks(dist, torch, sum(ms64)) * 1e-3)
@@ -744,7 +801,7 @@ def main():
     for i, (g_, f_, s_, st_) in enumerate(lanes):  # warm the second lane
         with torch.cuda.stream(st_):
             f_.copy_(host_in, non_blocking=True)
-            g_.step(f_, s_, times[i], wl.dt, 1, stream=st_)
+            g_.step_out(f_, s_, times[i], wl.dt, 1, stream=st_)
             times[i] += wl.dt
     torch.cuda.synchronize()
     _barrier(dist, torch)
@@ -758,8 +815,8 @@ def main():
         g_, f_, s_, st_ = lanes[i]
         with torch.cuda.stream(st_):
             f_.copy_(host_in, non_blocking=True)
-            g_.step(f_, s_, times[i], wl.dt, 1, stream=st_)
-            host_out[i].copy_(f_, non_blocking=True)
+            g_.step_out(f_, s_, times[i], wl.dt, 1, stream=st_)
+            host_out[i].copy_(s_, non_blocking=True)
         times[i] += wl.dt
     for _, _, _, st_ in lanes:
         stream.wait_stream(st_)
@@ -788,11 +845,11 @@ def main():
     # the configured arrival rate offers several times what the device can serve (the FP64 jobs
     # alone take most of it), so its latencies are queueing times; the same trace at a rate the
     # device sustains shows the service latency
-    serving_light = (serving_leg(max(args.serve_jobs // 3, 1), rank, ws, rate_hz=12.0)
+    serving_light = (serving_leg(min(args.serve_jobs, 100), rank, ws, rate_hz=12.0)
                      if (not args.no_extra and args.serve_jobs > 0) else None)
     # the same overloaded trace admitted in arrival order without a cap: every job shares the device
     # until the end (context for the policy's effect; same throughput)
-    serving_fifo = (serving_leg(args.serve_jobs, rank, ws, policy="fifo", max_active=4096)
+    serving_fifo = (serving_leg(min(args.serve_jobs, 300), rank, ws, policy="fifo", max_active=4096)
                     if (not args.no_extra and args.serve_jobs > 0) else None)
 
     if rank != 0:
@@ -807,17 +864,19 @@ def main():
         "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "swirl2d_1024x1024_3fields", "n": N_SIDE, "fields": NFIELDS, "cfl": 5, "steps_per_call": 1,
+                   "call": "sl_step_out (one full step out of place; input and result planes swap each step)",
                    "newton": "f32 with f64 re-solve of near-degenerate targets", "max_order": 1,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
+        "in_place_sl_step": in_place,
         "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": sum(ms64) / args.fp64_steps,
                  "path": "plain FP64 kernels (one thread per target, global gathers)",
                  "speedup_of_f32": value / fp64_value},
-        "roofline": {"bound": "hbm", "kernel": "remap_tiled2d_kernel, fused step (the headline's one launch per step)",
+        "roofline": {"bound": "hbm", "kernel": "remap2d_tma_kernel<32x32>, fused step (the headline's one launch per step)",
                      "achieved": step_achieved, "peak": hbm, "unit": "GB/s", "frac": step_achieved / hbm,
                      "traffic": NCU_TRAFFIC["step_bytes_per_launch"] if valid else None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": step_bytes, "bytes_rule": "2 F T per node (24 B)",
                      "launch_ms": step_launch_ms, "timed_over": "the headline's timed steps"},
-        "roofline_remap": {"bound": "hbm", "kernel": "remap_tiled2d_kernel, plain (sl_remap_fields)",
+        "roofline_remap": {"bound": "hbm", "kernel": "remap2d_tma_kernel<32x32>, plain (sl_remap_fields)",
                            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                            "traffic": NCU_TRAFFIC["remap_bytes_per_launch"] if valid else None, "peak_kind": peak_kind,
                            "algorithmic_bytes_per_launch": alg_bytes, "bytes_rule": "d T + 2 F T per node (32 B)",
@@ -836,8 +895,8 @@ def main():
         "serving_sustained_rate": serving_light,
         "serving_fifo_uncapped": serving_fifo,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": plane_bytes, "d2h_bytes_per_step": plane_bytes,
-                "how": "each step: pinned host -> device copy, sl_step, device -> pinned host copy; steps rotate "
-                       "over three grids on three streams so copies overlap kernels"},
+                "how": "each step: pinned host -> device copy, sl_step_out, device -> pinned host copy; steps "
+                       "rotate over three grids on three streams so copies overlap kernels"},
         "gpu_launches": launches,
         "clocks": clocks,
         "diagnostics": {k: diag[k] for k in ("targets", "fail_locate", "fail_newton", "fail_fold", "hops_max",

@@ -337,11 +337,12 @@ static cudaError_t step_impl(sl_grid *g, const void *const *in, void *const *A, 
         nxt[q] = A[q];
     }
     // after a step: its destination is the next source, the other buffer the next destination
+    // (B may be NULL for a single out-of-place step: nothing is written after the last step)
     auto advance = [&]() {
         const bool wasA = nxt[0] == A[0];
         for (int q = 0; q < g->nfields; ++q) {
             cur[q] = nxt[q];
-            nxt[q] = wasA ? B[q] : A[q];
+            nxt[q] = wasA ? (B ? B[q] : nullptr) : A[q];
         }
     };
     cudaError_t e = cudaSuccess;

@@ -66,8 +66,8 @@ static cudaError_t launch_r2(const sl_grid *g, const void *D, void *D_next, doub
     R2Maps maps;
     memset(&maps, 0, sizeof(maps));
     bool tma = true;
-    for (int f = 0; f < g->nfields; ++f) tma = tma && encode_f32(&maps.f[f], in[f], n0, n1, Cfg::WX, Cfg::STRIP);
-    tma = tma && encode_f32(&maps.D, D, 2 * n0, n1, 2 * Cfg::WX, Cfg::STRIP);
+    for (int f = 0; f < g->nfields; ++f) tma = tma && encode_f32(&maps.f[f], in[f], n0, n1, Cfg::WX, Cfg::WY);
+    tma = tma && encode_f32(&maps.D, D, 2 * n0, n1, 2 * Cfg::WX, Cfg::WY);
     A.use_tma = tma ? 1 : 0;
     VelArgs<float> vn;
     memset(&vn, 0, sizeof(vn));

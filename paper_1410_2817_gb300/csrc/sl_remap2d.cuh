@@ -5,7 +5,7 @@
 //   1. start points s = j - D_j of the tile's targets and the box of their elements floor(s);
 //   2. the departure window -- that box widened by the walk slack, the cubic stencil (c-1 .. c+2)
 //      and the limiter's neighbours -- is copied to shared memory: the displacement and the field
-//      planes by cp.async.bulk.tensor box loads (8-row strips, one mbarrier, no multicast), or by
+//      planes by cp.async.bulk.tensor box loads (one box per plane, one mbarrier, no multicast), or by
 //      per-element asynchronous copies when the window crosses the periodic seam;
 //   3. one pass over the window computes every node's jump flags (Sec. 2.3) and rewrites the
 //      planar field values as float4 records (h0, h1, h2, flag bits), so that one 128-bit shared
@@ -37,7 +37,7 @@ struct R2Cfg {
     static constexpr int PX = TX / 2;          // target pairs per tile row
     static constexpr int ROWS = NT / PX;       // tile rows per pass
     static constexpr int PPT = TY / ROWS;      // pairs per thread
-    static constexpr int STRIP = 8;            // rows per TMA box
+    static constexpr int STRIP = 8;            // the window capacity's rows come in multiples of 8
     static constexpr int CH = 4;               // rows per work item of the flag pass
     static_assert(PX % 16 == 0 && NT % PX == 0 && TY % ROWS == 0, "bad remap2d tile");
     static_assert(WX % 4 == 0 && WY % STRIP == 0 && 2 * WX <= 256, "bad remap2d window");
@@ -51,8 +51,8 @@ typedef R2Cfg<64, 32, 512, 88, 48, 1> R2Wide;    // one CTA of 16 warps per SM
 typedef R2Cfg<32, 32, 256, 44, 48, 2> R2Square;  // two CTAs of 8 warps per SM
 
 struct R2Maps {
-    CUtensorMap f[3];  // field planes: FP32, dims (n0, n1), box (WX, 8)
-    CUtensorMap D;     // displacement as FP32 pairs: dims (2 n0, n1), box (2 WX, 8)
+    CUtensorMap f[3];  // field planes: FP32, dims (n0, n1), box (WX, WY)
+    CUtensorMap D;     // displacement as FP32 pairs: dims (2 n0, n1), box (2 WX, WY)
 };
 
 // window of one tile: origin, extent, and how it is staged
@@ -103,20 +103,32 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned pari
         : "memory");
     return ok != 0;
 }
+// as mbar_test, but a thread whose phase is not complete is suspended (issuing nothing) until it
+// completes or about `ns` nanoseconds pass
+__device__ __forceinline__ bool mbar_test_suspend(unsigned long long *bar, unsigned parity, unsigned ns)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for phase `parity` of the barrier, giving up after 0.2 s (a copy that never lands).
+// Wait for phase `parity` of the barrier, suspended between tests, giving up after 0.2 s (a copy
+// that never lands).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_test(bar, parity)) return true;
+        if (mbar_test_suspend(bar, parity, 20000u)) return true;
         if (global_ns() - t0 > 200000000ull) return false;
     }
 }
@@ -364,43 +376,37 @@ __device__ __noinline__ TargetOut slow_target2(const TileArgs &a, const Win2 w, 
 }
 
 // ---- the flag pass: planar staging -> float4 records with the flag bits -------------------------
+// Sec. 2.3 jump test from the two one-sided differences dp = h+ - h, dm = h - h+ of a node.
+__device__ __forceinline__ bool jump_dd(float dp, float dm, float thr)
+{
+    return fabsf(dp - dm) > thr * fmaxf(fabsf(dp), fabsf(dm));
+}
+
 // Records are written for the window's interior nodes (1 .. wx-2, 1 .. wy-2), whose four
-// neighbours are staged.  A work item is one column over CH rows (consecutive threads take
-// consecutive columns); it keeps the column's values of the previous and current rows in
-// registers and reads the row neighbours and the next row from the staging planes.
+// neighbours are staged.  Consecutive threads take consecutive interior nodes of the window (row by
+// row), so that every shared-memory read of a node and of its four neighbours, and every record
+// written, falls in distinct banks; each node reads its five values per field and writes one
+// 128-bit record.
 template <class Cfg, int NF>
 __device__ __forceinline__ void flag_pass(const Win2 &w, const float *stage, float4 *sR, float thr, bool limit)
 {
-    constexpr int WX = Cfg::WX, CH = Cfg::CH, PLANE = WX * Cfg::WY;
-    const int ncol = w.wx - 2;
-    const int nch = (w.wy - 2 + CH - 1) / CH;
-    const int items = ncol * nch;
-    for (int q = threadIdx.x; q < items; q += Cfg::NT) {
-        const int ch = q / ncol, x = 1 + (q - ch * ncol);
-        const int y0 = 1 + ch * CH, y1 = min(y0 + CH, w.wy - 1);
-        float up[NF], c[NF];
+    constexpr int WX = Cfg::WX, PLANE = WX * Cfg::WY;
+    const int iw = w.wx - 2, ni = iw * (w.wy - 2);
+    const float inv_iw = 1.f / (float)iw;
+    for (int q = threadIdx.x; q < ni; q += Cfg::NT) {
+        const int r = row_of(q, inv_iw);
+        const int o = (r + 1) * WX + (q - r * iw) + 1;  // the node's offset in a plane
+        float hv[3] = {0.f, 0.f, 0.f};
+        unsigned bits = 0u;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const float *p = stage + f * PLANE + (y0 - 1) * WX + x;
-            up[f] = p[0];
-            c[f] = p[WX];
+            const float *p = stage + f * PLANE + o;
+            const float c = p[0];
+            hv[f] = c;
+            // Sec. 2.3 along x and along y: flagged where |dp - dm| > thr max(|dp|, |dm|)
+            if (limit && (jump_dd(p[1] - c, c - p[-1], thr) || jump_dd(p[WX] - c, c - p[-WX], thr))) bits |= 1u << f;
         }
-        for (int y = y0; y < y1; ++y) {
-            unsigned bits = 0u;
-            float vals[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const float *p = stage + f * PLANE + y * WX + x;
-                const float l = p[-1], r = p[1], dn = p[WX];
-                // Sec. 2.3 along y and along x: flagged where |dp - dm| > thr max(|dp|, |dm|)
-                if (limit && (jump_test<float>(up[f], c[f], dn, thr) || jump_test<float>(l, c[f], r, thr)))
-                    bits |= 1u << f;
-                vals[f] = c[f];
-                up[f] = c[f];
-                c[f] = dn;
-            }
-            sR[y * WX + x] = make_float4(vals[0], vals[1], vals[2], __uint_as_float(bits));
-        }
+        sR[o] = make_float4(hv[0], hv[1], hv[2], __uint_as_float(bits));
     }
 }
 
@@ -412,18 +418,17 @@ template <class Cfg, int NF>
 __device__ __forceinline__ void stage_window2(const R2Args &A, const R2Maps &maps, const Win2 &w, float *stage,
                                               float2 *sD, unsigned long long *bar)
 {
-    constexpr int WX = Cfg::WX, PLANE = WX * Cfg::WY, S = Cfg::STRIP;
+    constexpr int WX = Cfg::WX, PLANE = WX * Cfg::WY;
     if (w.mode == 1) {
-        if (threadIdx.x == 0) {
-            const int ns = (w.wy + S - 1) / S;
-            mbar_arrive_tx(bar, (unsigned)(ns * S * WX * 4 * (NF + 2)));
-            for (int s = 0; s < ns; ++s) {
-                const int y = w.loy + s * S;
-#pragma unroll
-                for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * PLANE + s * S * WX, &maps.f[f], w.lox, y, bar);
-                tma_load_2d(sD + s * S * WX, &maps.D, 2 * w.lox, y, bar);
-            }
-        }
+        // one box of WX x WY per tensor, each issued by its own lane of warp 0 (lane 0 arms the
+        // barrier first; the other lanes' copies follow after the warp's shuffle)
+        const int lane = threadIdx.x;
+        if (lane == 0) mbar_arrive_tx(bar, (unsigned)(Cfg::WY * WX * 4 * (NF + 2)));
+        if (threadIdx.x < 32) __syncwarp();
+        if (lane < NF)
+            tma_load_2d(stage + lane * PLANE, &maps.f[lane], w.lox, w.loy, bar);
+        else if (lane == NF)
+            tma_load_2d(sD, &maps.D, 2 * w.lox, w.loy, bar);
     } else if (w.mode == 2) {
         const TileArgs &a = A.t;
         const int nwin = w.wx * w.wy;
@@ -519,46 +524,117 @@ __device__ __forceinline__ void reduce_window(const R2Args &A, int mnx, int mny,
     }
 }
 
+// The fast path of one target (Sec. 2.2, eq. mapping1, Sec. 2.3, eq. multiZ), without branches:
+// the refined start (one fixed-point step s <- j - D(s), D bilinear in the staged window), the
+// element's vertices relative to the target, Newton from the linear part's solution with one
+// iteration, the element test and the stencil sum.  This is the first hop of walk_fast2 /
+// walk2w<float> when Newton converges in one iteration, so a target gets the same element,
+// coordinates and value on either path.  Every shared-memory index is clamped into its buffer, so
+// the whole computation runs unconditionally (two targets interleave freely); the result is valid
+// unless the element or its stencil leaves the staged window, the inversion needs more than one
+// iteration, meets a non-positive or nearly degenerate Jacobian, or lands outside the element --
+// such a target takes the general path.
+template <class Cfg, int NF>
+__device__ __forceinline__ bool fast_target(const Win2 &w, int base, const float2 *sD, const float4 *sR, int jx,
+                                            int jy, float2 s, bool limit, bool lin_only, float v[3], unsigned &nlin)
+{
+    constexpr int WX = Cfg::WX;
+    // refined start
+    const float fsx = floorf(s.x), fsy = floorf(s.y);
+    const int cx = (int)fsx, cy = (int)fsy;
+    // (a staged window is at least 9 nodes wide and high, so the unsigned bounds below do not wrap;
+    // an unstaged one has extent 0 and must be excluded first)
+    const bool in0 = w.mode != 0 && (unsigned)(cx - w.lox) < (unsigned)(w.wx - 1) &&
+                     (unsigned)(cy - w.loy) < (unsigned)(w.wy - 1);
+    const int i0 = in0 ? cy * WX + cx - base : 0;
+    const float fx = s.x - fsx, fy = s.y - fsy;
+    const float2 q00 = sD[i0], q10 = sD[i0 + 1], q01 = sD[i0 + WX], q11 = sD[i0 + WX + 1];
+    const float bx = fmaf(fx, q10.x - q00.x, q00.x), by = fmaf(fx, q10.y - q00.y, q00.y);
+    const float dx = fmaf(fy, fmaf(fx, q11.x - q01.x, q01.x) - bx, bx);
+    const float dy = fmaf(fy, fmaf(fx, q11.y - q01.y, q01.y) - by, by);
+    const float rx = (float)jx - dx, ry = (float)jy - dy;
+    const bool near = fabsf(rx - s.x) < 4.f && fabsf(ry - s.y) < 4.f;  // false for NaN
+    const int ex = near ? (int)floorf(rx) : cx, ey = near ? (int)floorf(ry) : cy;
+    // the element and its stencil (nodes ex-1 .. ex+2) in the flagged part of the window
+    const bool in1 = in0 && (unsigned)(ex - w.lox - 2) <= (unsigned)(w.wx - 6) &&
+                     (unsigned)(ey - w.loy - 2) <= (unsigned)(w.wy - 6);
+    const int e0 = in1 ? ey * WX + ex - base : WX + 1;
+    const float2 d0 = sD[e0], d1 = sD[e0 + 1], d2 = sD[e0 + WX], d3 = sD[e0 + WX + 1];
+    const float rx0 = (float)(ex - jx), rx1 = (float)(ex + 1 - jx);
+    const float ry0 = (float)(ey - jy), ry1 = (float)(ey + 1 - jy);
+    const float p0x = rx0 + d0.x, p0y = ry0 + d0.y, p1x = rx1 + d1.x, p1y = ry0 + d1.y;
+    const float p2x = rx0 + d2.x, p2y = ry1 + d2.y, p3x = rx1 + d3.x, p3y = ry1 + d3.y;
+    // Newton (the arithmetic of newton_solve2<float>, one iteration)
+    const float ax = p1x - p0x, ay = p1y - p0y, bxx = p2x - p0x, byy = p2y - p0y;
+    const float exx = p3x - p1x - p2x + p0x, eyy = p3y - p1y - p2y + p0y;
+    const float det0 = ax * byy - bxx * ay;
+    const float inv0 = recip_t(det0);
+    float xs = -(p0x * byy - p0y * bxx) * inv0;
+    float xt = -(ax * p0y - ay * p0x) * inv0;
+    const float j11 = ax + xt * exx, j21 = ay + xt * eyy;
+    const float j12 = bxx + xs * exx, j22 = byy + xs * eyy;
+    const float st = xs * xt;
+    const float gx = p0x + xs * ax + xt * bxx + st * exx;
+    const float gy = p0y + xs * ay + xt * byy + st * eyy;
+    const float det = j11 * j22 - j12 * j21;
+    const float inv = recip_t(det);
+    const float u0 = (gx * j22 - gy * j12) * inv;
+    const float u1 = (j11 * gy - j21 * gx) * inv;
+    xs -= u0;
+    xt -= u1;
+    const bool conv = det0 > 0.f && det > 0.f && fmaxf(fabsf(u0), fabsf(u1)) <= SL_NEWTON_TOL_F32;
+    const bool degen = det < SL_DEGENERATE * ((fabsf(j11) + fabsf(j21)) * (fabsf(j12) + fabsf(j22)));
+    const float slack = SL_SLACK_F32;
+    const bool inside = xs >= -slack && xs <= 1.f + slack && xt >= -slack && xt <= 1.f + slack;
+    const bool ok = in1 && conv && !degen && inside;
+    // records of the stencil (a block of the buffer's first rows when the target is not valid)
+    const int t0 = in1 ? (ey - 1) * WX + (ex - 1) - base : 0;
+    stencil_sum<WX, NF>(sR + t0, xs, xt, limit, lin_only, v, nlin);
+    return ok;
+}
+
 // Phase 4 of one tile: every target of the thread; general-path targets after the loop.
 template <class Cfg, int NF>
 __device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0, const Win2 &w, const float2 *sD,
                                               const float4 *sR, const float2 *S, LocalCounters &cnt)
 {
-    constexpr int WX = Cfg::WX;
     const bool limit = a.max_order >= 1 && a.thr >= 0.f;
     const bool lin_only = a.max_order == 0;
+    const int base = w.loy * Cfg::WX + w.lox;
     if (w.mode == 0 && threadIdx.x == 0) cnt.fallback += 1;
-    unsigned slow = 0u;
+    unsigned slow = 0u, nfast = 0u, nlin_sum = 0u;
+    // the two targets of a tile row (both halves) together: independent work to interleave
 #pragma unroll 1
-    for (int q = 0; q < 2 * Cfg::PPT; ++q) {
-        const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
-        if (jx >= a.n0 || jy >= a.n1) continue;
-        const float2 s = S[q * Cfg::NT + threadIdx.x];
-        int ex, ey;
-        refined_start2<Cfg>(w, sD, jx, jy, s.x, s.y, ex, ey);
-        int hops = 0, iters = 0;
-        float xi0 = 0.f, xi1 = 0.f;
-        bool good = w.mode != 0 && walk_fast2<Cfg>(w, sD, a.walk_max, a.max_iter, jx, jy, ex, ey, xi0, xi1, hops, iters);
-        const int rx = ex - w.lox, ry = ey - w.loy;
-        good = good && rx >= 2 && rx <= w.wx - 4 && ry >= 2 && ry <= w.wy - 4;
-        if (good) {
-            float v[3];
-            unsigned nlin;
-            stencil_sum<WX, NF>(sR + (ry - 1) * WX + (rx - 1), xi0, xi1, limit, lin_only, v, nlin);
-            const long long jj = (long long)jy * a.n0 + jx;
+    for (int k = 0; k < Cfg::PPT; ++k) {
+        const int jy = target_y<Cfg>(y0, k);
+        const int jxa = target_x<Cfg>(x0, 0), jxb = target_x<Cfg>(x0, 1);
+        const float2 sa = S[(2 * k) * Cfg::NT + threadIdx.x], sb = S[(2 * k + 1) * Cfg::NT + threadIdx.x];
+        float va[3], vb[3];
+        unsigned na = 0u, nb = 0u;
+        const bool oka = fast_target<Cfg, NF>(w, base, sD, sR, jxa, jy, sa, limit, lin_only, va, na);
+        const bool okb = fast_target<Cfg, NF>(w, base, sD, sR, jxb, jy, sb, limit, lin_only, vb, nb);
+        const bool ina = jxa < a.n0 && jy < a.n1, inb = jxb < a.n0 && jy < a.n1;
+        const bool fa = ina && oka && w.mode != 0, fb = inb && okb && w.mode != 0;
+        const long long jj = (long long)jy * a.n0 + jxa;
+        const int hb = Cfg::PX;  // the second target is PX columns to the right
 #pragma unroll
-            for (int f = 0; f < NF; ++f) a.out[f][jj] = v[f];
-            cnt.targets += 1;
-            cnt.hops += hops;
-            cnt.hops_max = max(cnt.hops_max, (unsigned)hops);
-            cnt.iters += iters;
-            cnt.iters_max = max(cnt.iters_max, (unsigned)iters);
-            cnt.oh0 += nlin;
-            cnt.oh1 += NF - nlin;
-        } else {
-            slow |= 1u << q;
+        for (int f = 0; f < NF; ++f) {
+            if (fa) a.out[f][jj] = va[f];
+            if (fb) a.out[f][jj + hb] = vb[f];
         }
+        nfast += (fa ? 1u : 0u) + (fb ? 1u : 0u);
+        nlin_sum += (fa ? na : 0u) + (fb ? nb : 0u);
+        slow |= ((ina && !fa) ? 1u : 0u) << (2 * k);
+        slow |= ((inb && !fb) ? 1u : 0u) << (2 * k + 1);
     }
+    // fast targets: one hop, one Newton iteration each
+    cnt.targets += nfast;
+    cnt.hops += nfast;
+    cnt.iters += nfast;
+    cnt.hops_max = max(cnt.hops_max, nfast ? 1u : 0u);
+    cnt.iters_max = max(cnt.iters_max, nfast ? 1u : 0u);
+    cnt.oh0 += nlin_sum;
+    cnt.oh1 += NF * nfast - nlin_sum;
 #pragma unroll 1
     for (int q = 0; slow != 0u; ++q, slow >>= 1) {
         if (!(slow & 1u)) continue;
@@ -652,16 +728,21 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
         const int p = k & 1;
         const int tr = t / A.tiles_x, x0 = (t - tr * A.tiles_x) * TX, y0 = tr * TY;
         const int tn = t + G;
-        // start points and window of the next tile (its displacements are in registers)
+        // start points of the next tile (its displacements are in registers) into the box
         if (tn < A.ntiles) {
             const int trn = tn / A.tiles_x;
             int mnx, mny, mxx, mxy;
             start_points2<Cfg>(a, (tn - trn * A.tiles_x) * TX, trn * TY, dj, spts + (p ^ 1) * 2 * PPT * Cfg::NT, mnx, mny,
                                mxx, mxy);
-            reduce_window<Cfg>(A, mnx, mny, mxx, mxy, box, W, p ^ 1);
-            if (tn + G < A.ntiles) {
-                const int t2 = tn + G, tr2 = t2 / A.tiles_x;
-                load_dj<Cfg>(a, (t2 - tr2 * A.tiles_x) * TX, tr2 * TY, dj);
+            mnx = __reduce_min_sync(0xffffffffu, mnx);
+            mny = __reduce_min_sync(0xffffffffu, mny);
+            mxx = __reduce_max_sync(0xffffffffu, mxx);
+            mxy = __reduce_max_sync(0xffffffffu, mxy);
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&box[0], mnx);
+                atomicMin(&box[1], mny);
+                atomicMax(&box[2], mxx);
+                atomicMax(&box[3], mxy);
             }
         }
         // this tile's window
@@ -669,12 +750,17 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
             atomicAdd(A.timeouts, 1ull);
             abort_flag = 1;
         }
-        __syncthreads();
+        __syncthreads();  // the box is complete, the window has landed
         if (abort_flag) break;
         // the phase has completed: every thread observes it once, which orders the copies' data
         // before its own reads
         (void)mbar_test(&bar[p], (phase >> p) & 1u);
         phase ^= 1u << p;
+        if (threadIdx.x == 0 && tn < A.ntiles) {
+            W[p ^ 1] = window2<Cfg>(box[0], box[1], box[2], box[3], a.n0, a.n1, A.use_tma != 0);
+            box[0] = box[1] = INT_MAX;
+            box[2] = box[3] = INT_MIN;
+        }
         const Win2 w = W[p];
         if (w.mode != 0) flag_pass<Cfg, NF>(w, stage, rec, a.thr, a.max_order >= 1 && a.thr >= 0.f);
         fence_proxy_async();  // the staging planes' reads before the next box copies overwrite them
@@ -682,6 +768,10 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
         // the staging planes are free: copy the next tile's window while this one is computed
         if (tn < A.ntiles) {
             stage_window2<Cfg, NF>(A, maps, W[p ^ 1], stage, dwin + (p ^ 1) * WX * WY, &bar[p ^ 1]);
+            if (tn + G < A.ntiles) {
+                const int t2 = tn + G, tr2 = t2 / A.tiles_x;
+                load_dj<Cfg>(a, (t2 - tr2 * A.tiles_x) * TX, tr2 * TY, dj);
+            }
         }
         if (FUSED && a.D_next != nullptr) integrate_next2<Cfg>(a, vn, x0, y0);
         compute_tile2<Cfg, NF>(a, x0, y0, w, dwin + p * WX * WY, rec, spts + p * 2 * PPT * Cfg::NT, cnt);

@@ -327,8 +327,14 @@ def serve_trace(jobs: Sequence, fields_of: Callable[[object], np.ndarray], budge
     offered = sum(j.workload.nnodes * j.workload.steps for j in jobs)
     last_arrival = max((j.arrival_s for j in jobs), default=0.0)
     by_kind = collections.defaultdict(list)
+    work_kind = collections.defaultdict(float)
+    offered_kind = collections.defaultdict(float)
     for st in done:
-        by_kind[f"{st.job.workload.dim}d_{st.job.dtype}"].append(st.finished_s - st.job.arrival_s)
+        kind = f"{st.job.workload.dim}d_{st.job.dtype}"
+        by_kind[kind].append(st.finished_s - st.job.arrival_s)
+        work_kind[kind] += st.job.workload.nnodes * st.job.workload.steps
+    for j in jobs:
+        offered_kind[f"{j.workload.dim}d_{j.dtype}"] += j.workload.nnodes * j.workload.steps
     return {
         "jobs": len(jobs), "completed": len(done), "rejected": sum(1 for s in sched.done.values() if s.rejected),
         "latency_s": percentiles(lat), "mean_latency_s": float(np.mean(lat)) if lat else None,
@@ -336,6 +342,12 @@ def serve_trace(jobs: Sequence, fields_of: Callable[[object], np.ndarray], budge
         "makespan_s": makespan, "lane_steps": lane_steps, "node_steps": total,
         "achieved_node_updates_per_s": total / makespan if makespan > 0 else None,
         "offered_node_updates_per_s": offered / last_arrival if last_arrival > 0 else None,
+        # per job kind: node-updates offered per second of arrivals, and completed per second of
+        # the whole run (the kinds share the device, so these add up to the totals above)
+        "node_updates_per_s_by_kind": {
+            k: {"offered": offered_kind[k] / last_arrival if last_arrival > 0 else None,
+                "achieved": work_kind[k] / makespan if makespan > 0 else None}
+            for k in sorted(offered_kind)},
         "peak_active": sched.peak_active, "peak_bytes": sched.peak_used, "budget_bytes": budget_bytes,
         "policy": policy, "max_active": max_active,
         "results": results if keep_results else None,
