@@ -43,7 +43,7 @@ FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at 1024^2 (3 fields) of the fused step
 # kernel (the headline's only launch) and of the plain remap kernel (sl_remap_fields), from the ncu
 # captures summarised in profiles/; valid only for the kernel source they were taken on.
-NCU_TRAFFIC = {"step_bytes_per_launch": 21063040, "remap_bytes_per_launch": 21037568, "source_sha": "40e8830465f80f63"}
+NCU_TRAFFIC = {"step_bytes_per_launch": 33100800, "remap_bytes_per_launch": 21041408, "source_sha": "027381b64628d107"}
 
 
 def warm_flushed(flush, step, n=3):
@@ -268,13 +268,14 @@ def run_reference(args):
 
 
 def kernel_only(args):
-    """Launch only sl_remap_fields or sl_step (FP32 production path) on the swirl workload (Z1, or
-    Z2 for remap_z2), sl_remap_fields on the 3-D deformation flow, or sl_step on the Kelvin wave
-    (nlsw), for profilers; prints the mean CUDA-event time per call."""
+    """Launch only sl_remap_fields or sl_step (FP32 production path; step64: the plain FP64 path) on
+    the swirl workload (Z1, or Z2 for remap_z2), sl_remap_fields or sl_step on the 3-D deformation
+    flow (remap3d, step3d), or sl_step on the Kelvin wave (nlsw), for profilers; prints the mean
+    CUDA-event time per call."""
     import torch
     from paper_1410_2817_gb300 import build, inputs, sl
     build.build()
-    if args.mode == "remap3d":
+    if args.mode in ("remap3d", "step3d"):
         wl = inputs.workload_deform3d(args.n)
     elif args.mode == "nlsw":
         wl = inputs.workload_kelvin(args.n)
@@ -282,8 +283,9 @@ def kernel_only(args):
         wl = inputs.workload_swirl(args.n)
         if args.mode == "remap_z2":
             wl.max_order = 2
-    g = sl.grid_for(wl, sl.SL_F32)
-    f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
+    f64 = args.mode == "step64"
+    g = sl.grid_for(wl, sl.SL_F64 if f64 else sl.SL_F32)
+    f = torch.tensor(wl.fields, dtype=torch.float64 if f64 else torch.float32, device="cuda")
     out = torch.empty_like(f)
     if args.mode != "nlsw":
         g.advect(0.5, wl.dt)
@@ -343,13 +345,16 @@ def batched_leg(torch, sl, inputs, steps=50, tile_config=None, max_order=1):
 
 def deform3d_leg(torch, sl, inputs, steps=5):
     """3-D 256^3 deformation flow (T = 3, dt = 0.03), two fields, FP32 bulk with FP64 re-solves of
-    degenerate elements: `steps` full steps through sl_step, L2 flushed before each; and the same
-    with the quintic Z-spline (plain kernels: 6 x 6 x 6 taps per field)."""
+    degenerate elements: `steps` full steps through sl_step, L2 flushed before each; the same steps
+    with every target's element map inverted in FP64 (SL_NEWTON_F64 on the blocked kernel), with the
+    largest difference of its fields from the mixed run's; and the quintic Z-spline (plain kernels:
+    6 x 6 x 6 taps per field)."""
     out = {}
-    for name, mo, nsteps in (("cubic", 1, steps), ("quintic_plain", 2, 2)):
+    for name, mo, nsteps, newton in (("cubic", 1, steps, sl.SL_NEWTON_MIXED), ("newton_f64", 1, steps, sl.SL_NEWTON_F64),
+                                     ("quintic_plain", 2, 2, sl.SL_NEWTON_MIXED)):
         wl = inputs.workload_deform3d(256, steps=nsteps)
         wl.max_order = mo
-        g = sl.grid_for(wl, sl.SL_F32)
+        g = sl.grid_for(wl, sl.SL_F32, newton_mode=newton)
         f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
         s = torch.empty_like(f)
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -375,7 +380,17 @@ def deform3d_leg(torch, sl, inputs, steps=5):
         tot = sum(a.elapsed_time(b) for a, b in ms)
         out[name] = {"workload": f"deform3d 256^3, 2 fields, FP32, max_order {mo}",
                      "value": wl.nnodes * nsteps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / nsteps}
-        if mo == 1:
+        if name == "cubic":
+            f_mixed = f.clone()
+        if name == "newton_f64":
+            # the same 3 + nsteps steps from the same fields as the mixed run
+            dd = (f - f_mixed).abs()
+            out[name]["inversion"] = "FP64 Newton for every target (blocked kernel)"
+            out[name]["max_abs_diff_vs_mixed"] = float(dd.max())
+            out[name]["l1_rel_diff_vs_mixed"] = float(dd.sum() / f_mixed.abs().sum())
+            out[name]["steps_compared"] = 3 + nsteps
+            out[name]["time_ratio_vs_mixed"] = (tot / nsteps) / out["cubic"]["ms_per_step"]
+        if name in ("cubic", "newton_f64"):
             # sl_remap_fields alone (box flags: two passes; the blocked remap), L2 flushed
             g.advect(t, wl.dt)
             o = torch.empty_like(f)
@@ -389,6 +404,10 @@ def deform3d_leg(torch, sl, inputs, steps=5):
                 rm.append((a, b))
             torch.cuda.synchronize()
             remap_ms = sum(a.elapsed_time(b) for a, b in rm) / nsteps
+            if name == "newton_f64":
+                out[name]["remap_ms"] = remap_ms
+                g.close()
+                continue
             hbm, kind = _peaks()
             F, N3 = wl.nfields, wl.nnodes
             step_bytes, remap_bytes = N3 * 2 * F * 4, N3 * (3 * 4 + 2 * F * 4)
@@ -406,6 +425,7 @@ def deform3d_leg(torch, sl, inputs, steps=5):
                                            "bytes_rule": "d T + 2 F T per node (28 B)", "launch_ms": remap_ms}
         g.close()
     res = dict(out["cubic"])
+    res["newton_f64"] = out["newton_f64"]
     res["quintic_plain"] = out["quintic_plain"]
     return res
 
@@ -638,7 +658,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, 3-D and serving legs")
     ap.add_argument("--serve-jobs", type=int, default=2000, help="jobs of the served trace (0: skip)")
-    ap.add_argument("--mode", default="full", choices=["full", "remap", "step", "remap3d", "remap_z2", "nlsw"],
+    ap.add_argument("--mode", default="full", choices=["full", "remap", "step", "step64", "remap3d", "step3d", "remap_z2", "nlsw"],
                     help="remap/step: only launch that call --steps times (for profilers); prints its timing")
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
     args = ap.parse_args()

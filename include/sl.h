@@ -115,7 +115,9 @@ typedef struct {
     int velocity_kind;              /* SL_VEL_*                                                      */
     const double *velocity_params;  /* host array, copied by sl_create_grid                          */
     int n_velocity_params;
-    int newton_mode;                /* SL_NEWTON_F64 (any dtype) or SL_NEWTON_MIXED (SL_F32 only)    */
+    int newton_mode;                /* SL_NEWTON_F64 (any dtype) or SL_NEWTON_MIXED (SL_F32 only).
+                                       SL_F32 with SL_NEWTON_F64 inverts every target in FP64: on
+                                       the blocked kernel in 3-D, on the plain kernels in 2-D   */
     int newton_max_iter;            /* <= 0 selects 8                                                */
     int walk_max;                   /* <= 0 selects 64                                               */
     int fail_policy;                /* SL_FAIL_KEEP or SL_FAIL_ERROR                                  */
@@ -238,8 +240,8 @@ sl_status sl_moments_noalloc(int dim, const int64_t n[3], const double lo[3], co
                              const void *field, int pmax, double *host_out, void *stream);
 
 /* ---- Batches: many independent 2-D FP32 grids advanced together ---------------------------
- * A batch advances count grids (created with sl_create_grid, 2-D, SL_F32, the same nfields <= 4,
- * backward walk start, an analytic velocity with any integrator and sub-step count; either all of
+ * A batch advances count grids (created with sl_create_grid, 2-D, SL_F32 with SL_NEWTON_MIXED, the
+ * same nfields <= 4, backward walk start, an analytic velocity with any integrator and sub-step count; either all of
  * max_order <= 1 or all quintic, max_order 2, whose tiles are 32 x 32 whatever tile_config) by the
  * same number of steps with one persistent launch per step over a work-list of (grid, tile)
  * items: each item is the single-grid tiled step of that tile (Sec. 2.1-2.3, eq. multiZ, eq. vel).  Grids keep their own workspaces (displacements and

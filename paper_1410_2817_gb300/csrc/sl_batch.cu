@@ -33,24 +33,14 @@ struct BatchGrid {
     int tiles_x, tile_base;
 };
 
-// cos(pi t / period) at the stage times of every trajectory sub-step of a step starting at t (the
-// single-grid host code fills the same table): sub-step s starts at t + s h, h = dt / substeps, and
-// its stages sit at c = (0, 1/2, 1) of h for RK4, (0, 1/3, 3/4) for Williamson's RK3
+// cos(pi t / period) at the stage times of every trajectory sub-step of a step starting at t, by
+// the single-grid host code's own function (stage_time_factors); zero for a steady flow
 __device__ __forceinline__ void stage_factors(const BatchGrid &g, double t, float *ct)
 {
-    const int ns = g.vel.substeps;
     if (g.period > 0.0) {
-        const double h = g.dt / ns;
-        const bool w3 = g.vel.integrator == SL_WRK3;
-        const double c1 = w3 ? 1.0 / 3.0 : 0.5, c2 = w3 ? 0.75 : 1.0;
-        for (int st = 0; st < ns; ++st) {
-            const double ts = t + (double)st * h;
-            ct[3 * st + 0] = (float)cospi(ts / g.period);
-            ct[3 * st + 1] = (float)cospi((ts + c1 * h) / g.period);
-            ct[3 * st + 2] = (float)cospi((ts + c2 * h) / g.period);
-        }
+        stage_time_factors<float>(t, g.dt, g.vel.substeps, g.vel.integrator, g.period, ct);
     } else {
-        for (int q = 0; q < 3 * ns; ++q) ct[q] = 0.f;
+        for (int q = 0; q < 3 * g.vel.substeps; ++q) ct[q] = 0.f;
     }
 }
 
@@ -170,7 +160,7 @@ __global__ void __launch_bounds__(Cfg::NT)
         for (int q = threadIdx.x; q < Cfg::TX * Cfg::TY; q += Cfg::NT) {
             const int jx = tx * Cfg::TX + q % Cfg::TX, jy = ty * Cfg::TY + q / Cfg::TX;
             if (jx >= sg.base.n0 || jy >= sg.base.n1) continue;
-            float X[3] = {sv.lo[0] + (float)jx * sv.dx[0], sv.lo[1] + (float)jy * sv.dx[1], 0.f}, d[3];
+            float X[3] = {node_position(sv.lo[0], jx, sv.dx[0]), node_position(sv.lo[1], jy, sv.dx[1]), 0.f}, d[3];
             trajectory_cells<float, 2>(sv, X, d);
             D[(long long)jy * sg.base.n0 + jx] = make_float2(d[0], d[1]);
         }
@@ -265,7 +255,8 @@ struct sl_batch {
 // classical RK4 step per remap only
 static bool batch_eligible(const sl_grid *g)
 {
-    return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.walk_start == SL_START_BACKWARD && !g->carried && !g->nlsw;
+    return g && g->dim == 2 && g->dtype == SL_F32 && g->desc.newton_mode == SL_NEWTON_MIXED &&
+           g->desc.walk_start == SL_START_BACKWARD && !g->carried && !g->nlsw;
 }
 
 // Tiles of quintic batches are the quintic kernel's 32 x 32 whatever the tile configuration.

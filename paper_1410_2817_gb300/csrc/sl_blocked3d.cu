@@ -305,7 +305,9 @@ __device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4],
     }
 }
 
-template <int NFM, bool FUSED>
+// N64: every target's element search and Newton inversion in FP64 (SL_NEWTON_F64) from the refined
+// start; otherwise in FP32 with an FP64 re-solve of failed or near-degenerate targets.
+template <int NFM, bool FUSED, bool N64>
 __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3Args a, const VelArgs<float> vn)
 {
     const Geo3 &g = a.g;
@@ -369,8 +371,9 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
         int hops = 0, iters = 0;
         float xf[3] = {0.f, 0.f, 0.f};
         bool degen = false;
-        int st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters, &degen);
-        if (st != ST_OK || degen) {
+        int st = ST_OK;
+        if (!N64) st = walk3<float>(g, a.D, a.max_iter, a.walk_max, j, c, xf, hops, iters, &degen);
+        if (N64 || st != ST_OK || degen) {
             const Resolve3 r = resolve3_f64(a.D, g.n0, g.n1, g.n2, a.max_iter, a.walk_max, j[0], j[1], j[2], st, c[0],
                                             c[1], c[2], c0[0], c0[1], c0[2]);
             st = r.st;
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             xf[2] = r.x2;
             hops += r.hops;
             iters += r.iters;
-            cnt.f64 += 1;
+            cnt.f64 += N64 ? 0 : 1;
         }
         cnt.targets = 1;
         cnt.hops = hops;
@@ -438,7 +441,8 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             }
         }
         if (FUSED && a.D_next != nullptr) {
-            float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], vn.lo[2] + (float)jz * vn.dx[2]};
+            float X[3] = {node_position(vn.lo[0], jx, vn.dx[0]), node_position(vn.lo[1], jy, vn.dx[1]),
+                          node_position(vn.lo[2], jz, vn.dx[2])};
             float d[3];
             trajectory_cells<float, 3>(vn, X, d);
             a.D_next[jj] = make_float4(d[0], d[1], d[2], 0.f);
@@ -479,6 +483,20 @@ cudaError_t launch_box_flags3d(const sl_grid *g, const void *const *in, uint8_t 
     return cudaGetLastError();
 }
 
+template <bool N64>
+static void launch_b3(int nfm, bool fused, dim3 grid, cudaStream_t s, const Blocked3Args &a, const VelArgs<float> &vn)
+{
+    if (fused) {
+        if (nfm == 2) remap_blocked3d_kernel<2, true, N64><<<grid, NT3, 0, s>>>(a, vn);
+        else if (nfm == 4) remap_blocked3d_kernel<4, true, N64><<<grid, NT3, 0, s>>>(a, vn);
+        else remap_blocked3d_kernel<8, true, N64><<<grid, NT3, 0, s>>>(a, vn);
+    } else {
+        if (nfm == 2) remap_blocked3d_kernel<2, false, N64><<<grid, NT3, 0, s>>>(a, vn);
+        else if (nfm == 4) remap_blocked3d_kernel<4, false, N64><<<grid, NT3, 0, s>>>(a, vn);
+        else remap_blocked3d_kernel<8, false, N64><<<grid, NT3, 0, s>>>(a, vn);
+    }
+}
+
 cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, const uint8_t *box, double t_next,
                              double dt, bool fused, const void *const *in, void *const *out, cudaStream_t s)
 {
@@ -503,14 +521,9 @@ cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, cons
     memset(&vn, 0, sizeof(vn));
     if (fused) vn = make_vel_args<float>(g, t_next, dt);
     const int nfm = g->nfields <= 2 ? 2 : g->nfields <= 4 ? 4 : 8;
-    if (fused) {
-        if (nfm == 2) remap_blocked3d_kernel<2, true><<<grid, NT3, 0, s>>>(a, vn);
-        else if (nfm == 4) remap_blocked3d_kernel<4, true><<<grid, NT3, 0, s>>>(a, vn);
-        else remap_blocked3d_kernel<8, true><<<grid, NT3, 0, s>>>(a, vn);
-    } else {
-        if (nfm == 2) remap_blocked3d_kernel<2, false><<<grid, NT3, 0, s>>>(a, vn);
-        else if (nfm == 4) remap_blocked3d_kernel<4, false><<<grid, NT3, 0, s>>>(a, vn);
-        else remap_blocked3d_kernel<8, false><<<grid, NT3, 0, s>>>(a, vn);
-    }
+    if (g->desc.newton_mode == SL_NEWTON_F64)
+        launch_b3<true>(nfm, fused, grid, s, a, vn);
+    else
+        launch_b3<false>(nfm, fused, grid, s, a, vn);
     return cudaGetLastError();
 }

@@ -19,6 +19,66 @@
 #define SL_MAX_VEL_PARAMS 80
 
 // ------------------------------------------------------------------------------------------------
+// time factor cos(pi t / period) of the swirl and deformation flows (eq. vel), computed by the same
+// operations on the host (single grids) and on the device (batches, from per-grid device times), so
+// that a grid in a batch sees the very factors it sees alone
+// ------------------------------------------------------------------------------------------------
+// cos(pi x): a = |x - 2 rint(x / 2)| in [0, 1]; cos(pi a) = sin(pi (1/2 - a)) = -cos(pi (1 - a))
+// folds it to an argument b in [0, 1/4] (both differences are exact); then the Taylor series of
+// cos(pi b) through (pi b)^18 or of sin(pi b) through (pi b)^17 (first neglected terms below 1e-19)
+// by Horner's rule with explicit fused multiply-adds.
+__host__ __device__ inline double cospi_time(double x)
+{
+    const double a = fabs(x - 2.0 * rint(0.5 * x));
+    const bool mid = a > 0.25 && a <= 0.75;
+    const double b = a <= 0.25 ? a : (mid ? 0.5 - a : 1.0 - a);
+    const double r = 3.141592653589793 * b, u = r * r;
+    double p;
+    if (mid) {  // sin(r) / r = sum (-1)^k u^k / (2k+1)!
+        p = 1.0 / 355687428096000.0;
+        p = fma(u, p, -1.0 / 1307674368000.0);
+        p = fma(u, p, 1.0 / 6227020800.0);
+        p = fma(u, p, -1.0 / 39916800.0);
+        p = fma(u, p, 1.0 / 362880.0);
+        p = fma(u, p, -1.0 / 5040.0);
+        p = fma(u, p, 1.0 / 120.0);
+        p = fma(u, p, -1.0 / 6.0);
+        p = fma(u, p, 1.0);
+        return r * p;
+    }
+    p = 1.0 / 6402373705728000.0;  // cos(r) = sum (-1)^k u^k / (2k)!
+    p = fma(u, p, -1.0 / 20922789888000.0);
+    p = fma(u, p, 1.0 / 87178291200.0);
+    p = fma(u, p, -1.0 / 479001600.0);
+    p = fma(u, p, 1.0 / 3628800.0);
+    p = fma(u, p, -1.0 / 40320.0);
+    p = fma(u, p, 1.0 / 720.0);
+    p = fma(u, p, -1.0 / 24.0);
+    p = fma(u, p, 0.5);
+    // the last step by hand: cos = 1 - u p with the sign of the fold
+    p = fma(-u, p, 1.0);
+    return a <= 0.25 ? p : -p;
+}
+
+// The time factors of one step of length dt from t: sub-step s starts at t_s = t + s h, h = dt /
+// substeps, its stages sit at t_s + c h with c = (0, 1/2, 1) for RK4 and (0, 1/3, 3/4) for
+// Williamson's RK3; ct[3 s + k] = cos(pi (t_s + c_k h) / period).
+template <typename T>
+__host__ __device__ inline void stage_time_factors(double t, double dt, int substeps, int integrator, double period,
+                                                   T *ct)
+{
+    const double h = dt / substeps;
+    const bool w3 = integrator == SL_WRK3;
+    const double c1 = w3 ? 1.0 / 3.0 : 0.5, c2 = w3 ? 0.75 : 1.0;
+    for (int st = 0; st < substeps; ++st) {
+        const double ts = fma((double)st, h, t);
+        ct[3 * st + 0] = (T)cospi_time(ts / period);
+        ct[3 * st + 1] = (T)cospi_time(fma(c1, h, ts) / period);
+        ct[3 * st + 2] = (T)cospi_time(fma(c2, h, ts) / period);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // argument blocks (passed by value)
 // ------------------------------------------------------------------------------------------------
 struct DevCounters {
@@ -274,9 +334,131 @@ __device__ __forceinline__ void trajectory_cells(const VelArgs<T> &v, const T X[
     if (DIM == 2) out[2] = T(0);
 }
 
+// a * b + c with one rounding, and a * b rounded alone (never contracted into a neighbouring add):
+// the trajectories below are inlined into several kernels, and each must round them the same way
+__device__ __forceinline__ float fma_rn_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn_t(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn_t(double a, double b) { return __dmul_rn(a, b); }
+
+// physical position lo + k dx of node k along one axis (one rounding, the same in every kernel)
+template <typename T>
+__device__ __forceinline__ T node_position(T lo, int k, T dx) { return fma_rn_t(T(k), dx, lo); }
+
+// sin(pi d), cos(pi d) of a small offset d from their Taylor series in r = pi d by Horner's rule
+// in u = r^2.  FP64: |d| <= 1/16 (|r| <= 0.2), through r^11 / r^12 (the first neglected term is
+// below 1e-19).  FP32: |d| <= 1/8 (|r| <= 0.4), through r^7 / r^8 (below 1e-9).
+template <typename T>
+__device__ __forceinline__ T small_offset_limit();
+template <>
+__device__ __forceinline__ double small_offset_limit<double>() { return 1.0 / 16.0; }
+template <>
+__device__ __forceinline__ float small_offset_limit<float>() { return 0.125f; }
+
+__device__ __forceinline__ void sincospi_small(double d, double *s, double *c)
+{
+    const double r = mul_rn_t(3.141592653589793238462643, d), u = mul_rn_t(r, r);
+    double ps = -1.0 / 39916800.0, pc = 1.0 / 479001600.0;
+    ps = fma_rn_t(u, ps, 1.0 / 362880.0);
+    ps = fma_rn_t(u, ps, -1.0 / 5040.0);
+    ps = fma_rn_t(u, ps, 1.0 / 120.0);
+    ps = fma_rn_t(u, ps, -1.0 / 6.0);
+    ps = fma_rn_t(u, ps, 1.0);
+    pc = fma_rn_t(u, pc, -1.0 / 3628800.0);
+    pc = fma_rn_t(u, pc, 1.0 / 40320.0);
+    pc = fma_rn_t(u, pc, -1.0 / 720.0);
+    pc = fma_rn_t(u, pc, 1.0 / 24.0);
+    pc = fma_rn_t(u, pc, -0.5);
+    *s = mul_rn_t(r, ps);
+    *c = fma_rn_t(u, pc, 1.0);
+}
+__device__ __forceinline__ void sincospi_small(float d, float *s, float *c)
+{
+    const float r = mul_rn_t(3.14159265358979f, d), u = mul_rn_t(r, r);
+    float ps = fma_rn_t(u, -1.f / 5040.f, 1.f / 120.f), pc = fma_rn_t(u, 1.f / 40320.f, -1.f / 720.f);
+    ps = fma_rn_t(u, ps, -1.f / 6.f);
+    ps = fma_rn_t(u, ps, 1.f);
+    pc = fma_rn_t(u, pc, 1.f / 24.f);
+    pc = fma_rn_t(u, pc, -0.5f);
+    *s = mul_rn_t(r, ps);
+    *c = fma_rn_t(u, pc, 1.f);
+}
+
+// sin(pi (x + d)), cos(pi (x + d)) with d = h k from sx = sin(pi x), cx = cos(pi x): by the
+// angle-addition formulas for a small offset d, else directly at x + h k (one rounding)
+template <typename T>
+__device__ __forceinline__ void sincospi_near(T sx, T cx, T x, T h, T k, T *s, T *c)
+{
+    const T d = mul_rn_t(h, k);
+    if (abs_t(d) <= small_offset_limit<T>()) {
+        T sd, cd;
+        sincospi_small(d, &sd, &cd);
+        *s = fma_rn_t(sx, cd, mul_rn_t(cx, sd));
+        *c = fma_rn_t(cx, cd, -mul_rn_t(sx, sd));
+    } else {
+        sincospi_t(fma_rn_t(h, k, x), s, c);
+    }
+}
+
+// The swirl and the 3-D deformation velocities of eq. (vel) (the formulas of `velocity`) from the
+// sines and cosines of pi x_a, every product rounded in the order written.
+template <typename T, int DIM>
+__device__ __forceinline__ void trig_velocity(int kind, const T s[3], const T c[3], T ct, T u[3])
+{
+    const T s2x = T(2) * mul_rn_t(s[0], c[0]), s2y = T(2) * mul_rn_t(s[1], c[1]);  // sin(2 pi x_a), exact doubling
+    if (kind == SL_VEL_SWIRL2D) {
+        u[0] = mul_rn_t(mul_rn_t(mul_rn_t(s[0], s[0]), s2y), ct);
+        u[1] = -mul_rn_t(mul_rn_t(mul_rn_t(s[1], s[1]), s2x), ct);
+        u[2] = T(0);
+    } else {
+        const T s2z = T(2) * mul_rn_t(s[2], c[2]);
+        u[0] = T(2) * mul_rn_t(mul_rn_t(mul_rn_t(mul_rn_t(s[0], s[0]), s2y), s2z), ct);
+        u[1] = -mul_rn_t(mul_rn_t(mul_rn_t(mul_rn_t(s[1], s[1]), s2z), s2x), ct);
+        u[2] = -mul_rn_t(mul_rn_t(mul_rn_t(mul_rn_t(s[2], s[2]), s2x), s2y), ct);
+    }
+}
+
+// One classical RK4 step of eq. (vel) for the swirl or the 3-D deformation flow: the sines and
+// cosines of pi X are evaluated once, those of each later stage's position X + delta from them
+// (sincospi_near); the stages, times and weights are rk4_cells' own, k1 + 2 k2 + 2 k3 + k4 summed
+// left to right.
+template <typename T, int DIM>
+__device__ __forceinline__ void rk4_trig_cells(const VelArgs<T> &v, const T X[3], T out[3])
+{
+    T s0[3] = {T(0), T(0), T(0)}, c0[3] = {T(1), T(1), T(1)}, s[3], c[3];
+    T k1[3], k2[3], k3[3], k4[3];
+    const T h = v.dt, hh = T(0.5) * v.dt, h6 = v.dt / T(6);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sincospi_t(X[a], &s0[a], &c0[a]);
+    trig_velocity<T, DIM>(v.kind, s0, c0, v.ct[0], k1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        s[a] = s0[a];
+        c[a] = c0[a];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sincospi_near(s0[a], c0[a], X[a], hh, k1[a], &s[a], &c[a]);
+    trig_velocity<T, DIM>(v.kind, s, c, v.ct[1], k2);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sincospi_near(s0[a], c0[a], X[a], hh, k2[a], &s[a], &c[a]);
+    trig_velocity<T, DIM>(v.kind, s, c, v.ct[1], k3);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sincospi_near(s0[a], c0[a], X[a], h, k3[a], &s[a], &c[a]);
+    trig_velocity<T, DIM>(v.kind, s, c, v.ct[2], k4);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const T sum = fma_rn_t(T(2), k3[a], fma_rn_t(T(2), k2[a], k1[a])) + k4[a];
+        out[a] = mul_rn_t(mul_rn_t(h6, sum), v.inv_dx[a]);
+    }
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ void rk4_cells(const VelArgs<T> &v, const T X[3], T out[3])
 {
+    if ((DIM == 2 && v.kind == SL_VEL_SWIRL2D) || (DIM == 3 && v.kind == SL_VEL_DEFORM3D)) {
+        rk4_trig_cells<T, DIM>(v, X, out);
+        return;
+    }
     T k1[3], k2[3], k3[3], k4[3], y[3] = {T(0), T(0), T(0)};
     const T h = v.dt, hh = T(0.5) * v.dt;
     velocity<T, DIM>(v, X, 0, k1);

@@ -37,15 +37,6 @@ GridArgs<T> make_grid_args(const sl_grid *g)
     return a;
 }
 
-static double cospi_host(double x)
-{
-    double r = x - 2.0 * nearbyint(0.5 * x);
-    double a = fabs(r);
-    if (a <= 0.25) return cos(M_PI * a);
-    if (a <= 0.75) return sin(M_PI * (0.5 - a));
-    return -cos(M_PI * (1.0 - a));
-}
-
 template <typename T>
 VelArgs<T> make_vel_args(const sl_grid *g, double t, double dt)
 {
@@ -57,22 +48,7 @@ VelArgs<T> make_vel_args(const sl_grid *g, double t, double dt)
     v.substeps = g->desc.trajectory_substeps > 0 ? g->desc.trajectory_substeps : 1;
     for (int q = 0; q < SL_MAX_VEL_PARAMS; ++q) v.p[q] = (T)g->vel_params[q];
     if (v.kind == SL_VEL_SWIRL2D || v.kind == SL_VEL_DEFORM3D) {
-        const double period = g->vel_params[0];
-        if (v.integrator == SL_RK4 && v.substeps == 1) {
-            v.ct[0] = (T)cospi_host(t / period);
-            v.ct[1] = (T)cospi_host((t + 0.5 * dt) / period);
-            v.ct[2] = (T)cospi_host((t + dt) / period);
-        } else {
-            // stage times of sub-step s: t_s + c h with t_s = t + s h, h = dt / substeps
-            const double h = dt / v.substeps;
-            const double c1 = v.integrator == SL_WRK3 ? 1.0 / 3.0 : 0.5, c2 = v.integrator == SL_WRK3 ? 0.75 : 1.0;
-            for (int st = 0; st < v.substeps; ++st) {
-                const double ts = t + (double)st * h;
-                v.ct[3 * st + 0] = (T)cospi_host(ts / period);
-                v.ct[3 * st + 1] = (T)cospi_host((ts + c1 * h) / period);
-                v.ct[3 * st + 2] = (T)cospi_host((ts + c2 * h) / period);
-            }
-        }
+        stage_time_factors<T>(t, dt, v.substeps, v.integrator, g->vel_params[0], v.ct);
     }
     for (int q = 0; q < 3; ++q) {
         v.lo[q] = (T)g->desc.lo[q];
@@ -172,7 +148,7 @@ __global__ void __launch_bounds__(256) advect_kernel(GridArgs<T> g, VelArgs<T> v
         node_coords<DIM>(i, g.n, k);
         T X[3] = {T(0), T(0), T(0)}, d[3];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) X[a] = v.lo[a] + T(k[a]) * v.dx[a];
+        for (int a = 0; a < DIM; ++a) X[a] = node_position(v.lo[a], k[a], v.dx[a]);
         trajectory_cells<T, DIM>(v, X, d);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) D[i * ds + a] = d[a];

@@ -669,7 +669,7 @@ __device__ __forceinline__ void integrate_next2(const TileArgs &a, const VelArgs
     for (int q = 0; q < 2 * Cfg::PPT; ++q) {
         const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
         if (jx >= a.n0 || jy >= a.n1) continue;
-        float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
+        float X[3] = {node_position(vn.lo[0], jx, vn.dx[0]), node_position(vn.lo[1], jy, vn.dx[1]), 0.f}, d[3];
         trajectory_cells<float, 2>(vn, X, d);
         reinterpret_cast<float2 *>(a.D_next)[(long long)jy * a.n0 + jx] = make_float2(d[0], d[1]);
     }

@@ -666,7 +666,7 @@ __device__ __forceinline__ void integrate_next(const TileArgs &a, const VelArgs<
     for (int k = 0; k < Cfg::TPT; ++k) {
         const int jx = x0 + tx, jy = y0 + ty + k * Cfg::ROWS;
         if (jx >= a.n0 || jy >= a.n1) continue;
-        float X[3] = {vn.lo[0] + (float)jx * vn.dx[0], vn.lo[1] + (float)jy * vn.dx[1], 0.f}, d[3];
+        float X[3] = {node_position(vn.lo[0], jx, vn.dx[0]), node_position(vn.lo[1], jy, vn.dx[1]), 0.f}, d[3];
         trajectory_cells<float, 2>(vn, X, d);
         reinterpret_cast<float2 *>(a.D_next)[(long long)jy * a.n0 + jx] = make_float2(d[0], d[1]);
     }

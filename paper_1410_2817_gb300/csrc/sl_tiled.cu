@@ -14,6 +14,9 @@ template <typename T>
 bool Launch<T>::tiled_supported(const sl_grid *g)
 {
     if (sizeof(T) != 4 || g->desc.walk_start != SL_START_BACKWARD) return false;
+    // the 2-D tile bodies invert in FP32 (FP64 re-solves only for failed or degenerate targets):
+    // an FP64 inversion of every target runs on the plain kernels
+    if (g->dim == 2 && g->desc.newton_mode == SL_NEWTON_F64) return false;
     if (g->desc.max_order > 1) return g->dim == 2 && tiled2d_smem_bytes_z2(g->nfields) <= 200 * 1024;
     if (g->dim == 3) return g->N < (1LL << 31);  // the blocked kernel forms 32-bit node offsets
     const int c = g->desc.tile_config;

@@ -636,6 +636,44 @@ def test_blocked3d_matches_generic_f32(sl, orc, case):
     assert diags["tiled"]["targets"] == int(np.prod(n))
 
 
+@pytest.mark.parametrize("newton_mode", ["mixed", "f64"])
+@pytest.mark.parametrize("case", ["deform3d_32", "ragged3d"])
+def test_blocked3d_f32_per_target(sl, orc, case, newton_mode):
+    """The blocked 3-D FP32 remap, target by target against the FP64 oracle on the same FP32
+    displacement and fields: each value within 2e-6 of the oracle's interpolation in the oracle's
+    element and order, or -- within FP32 rounding of a face or of a limiter threshold -- in the
+    neighbouring element or with the other order.  Both inversions: FP32 with FP64 re-solves of
+    failed or degenerate targets (mixed), and FP64 for every target (no re-solve is counted)."""
+    from tests import tiecheck
+    rng = np.random.default_rng(33)
+    if case == "deform3d_32":
+        n = (32, 32, 32)
+        og = _og(orc, 3, n, 2, velocity="deform3d", params=[3.0])
+        D, h = orc.advect(og, 0.4, 0.03), inputs.deform3d_fields(32)
+    else:
+        n = (19, 13, 11)
+        D = inputs.smooth_displacement(n, amplitude=0.3, seed=8, shift=(1.6, -2.2, 0.7))
+        h = np.stack([rng.standard_normal((11, 13, 19)).cumsum(axis=2) * 0.1, (rng.uniform(size=(11, 13, 19)) > 0.5) * 1.0,
+                      rng.standard_normal((11, 13, 19))])
+    D32, h32 = np.asarray(D, dtype=np.float32), np.asarray(h, dtype=np.float32)
+    nf = h32.shape[0]
+    nm = sl.SL_NEWTON_MIXED if newton_mode == "mixed" else sl.SL_NEWTON_F64
+    g = _gpu_grid(sl, 3, n, nf, sl.SL_F32, start="backward", kernel=sl.SL_KERNEL_TILED, newton_mode=nm)
+    hin = torch.tensor(h32, device=DEV)
+    hout = torch.empty_like(hin)
+    g.set_displacement(torch.tensor(D32, device=DEV))
+    g.remap(hin, hout)
+    torch.cuda.synchronize()
+    og = _og(orc, 3, n, nf, start="backward")
+    counts = tiecheck.f32_remap_targets(orc, og, D32, h32, hout.double().cpu().numpy(), 2e-6)
+    d = g.diagnostics()
+    assert counts["oracle_failed"] == 0 and d["fail_locate"] + d["fail_newton"] + d["fail_fold"] == 0
+    assert d["targets"] == int(np.prod(n))
+    if newton_mode == "f64":
+        assert d["newton_f64"] == 0
+    assert counts["face_ties"] + counts["limiter_ties"] <= 0.01 * d["targets"], counts
+
+
 def test_fp32_3d_step_accuracy(sl, orc):
     wl = inputs.workload_deform3d(32, steps=4)
     ref, got, g = _step_compare(sl, orc, wl, 4, sl.SL_F32, None)
