@@ -244,11 +244,10 @@ struct Blocked3Args {
 // eq. (multiZ) in 3-D for up to NFM fields: the 4x4x4 cubic (Z~1) sums and the trilinear (Z~0)
 // sums over the element's 8 vertices in one pass.  Fields run in pairs on packed FP32x2 FMAs
 // (each lane rounds as fmaf does); row offsets (32-bit: the blocked kernel takes grids below 2^31
-// nodes) are shared by all fields; with XIN (the stencil does not cross the x seam) the 4 taps of
-// a row sit at x0 .. x0+3.
-template <int NFM, bool XIN>
+// nodes) and the wrapped x offsets of the 4 taps are shared by all fields.
+template <int NFM>
 __device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4], const unsigned oy[4],
-                                         const unsigned oz[4], int x0, const float wc[3][4], const float xf[3],
+                                         const unsigned oz[4], const float wc[3][4], const float xf[3],
                                          float cub[NFM], float lin[NFM])
 {
     const float2 w0 = make_float2(wc[0][0], wc[0][0]), w1 = make_float2(wc[0][1], wc[0][1]);
@@ -266,20 +265,11 @@ __device__ __forceinline__ void tap_sums(const Blocked3Args &a, const int ox[4],
 #pragma unroll
             for (int ky = 0; ky < 4; ++ky) {
                 const unsigned ro = oz[kz] + oy[ky];
-                float2 t0, t1, t2, t3;
-                if (XIN) {
-                    const float *ra = ha + ro + x0, *rb = hb + ro + x0;
-                    t0 = make_float2(__ldg(ra), __ldg(rb));
-                    t1 = make_float2(__ldg(ra + 1), __ldg(rb + 1));
-                    t2 = make_float2(__ldg(ra + 2), __ldg(rb + 2));
-                    t3 = make_float2(__ldg(ra + 3), __ldg(rb + 3));
-                } else {
-                    const float *ra = ha + ro, *rb = hb + ro;
-                    t0 = make_float2(__ldg(ra + ox[0]), __ldg(rb + ox[0]));
-                    t1 = make_float2(__ldg(ra + ox[1]), __ldg(rb + ox[1]));
-                    t2 = make_float2(__ldg(ra + ox[2]), __ldg(rb + ox[2]));
-                    t3 = make_float2(__ldg(ra + ox[3]), __ldg(rb + ox[3]));
-                }
+                const float *ra = ha + ro, *rb = hb + ro;
+                const float2 t0 = make_float2(__ldg(ra + ox[0]), __ldg(rb + ox[0]));
+                const float2 t1 = make_float2(__ldg(ra + ox[1]), __ldg(rb + ox[1]));
+                const float2 t2 = make_float2(__ldg(ra + ox[2]), __ldg(rb + ox[2]));
+                const float2 t3 = make_float2(__ldg(ra + ox[3]), __ldg(rb + ox[3]));
                 float2 r = __fmul2_rn(w0, t0);
                 r = __ffma2_rn(w1, t1, r);
                 r = __ffma2_rn(w2, t2, r);
@@ -387,15 +377,15 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             iters += r.iters;
             cnt.f64 += N64 ? 0 : 1;
         }
-        cnt.targets = 1;
-        cnt.hops = hops;
-        cnt.hops_max = hops;
-        cnt.iters = iters;
-        cnt.iters_max = iters;
+        cnt.targets += 1;
+        cnt.hops += hops;
+        cnt.hops_max = max(cnt.hops_max, (unsigned)hops);
+        cnt.iters += iters;
+        cnt.iters_max = max(cnt.iters_max, (unsigned)iters);
         if (st != ST_OK) {
-            cnt.fl = st == ST_LOCATE;
-            cnt.fn = st == ST_NEWTON;
-            cnt.ff = st == ST_FOLD;
+            cnt.fl += st == ST_LOCATE;
+            cnt.fn += st == ST_NEWTON;
+            cnt.ff += st == ST_FOLD;
             for (int q = 0; q < a.nfields; ++q) a.f.out[q][jj] = __ldg(a.f.in[q] + jj);
         } else {
             float wc[3][4];
@@ -426,11 +416,10 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
                 }
                 if (a.max_order >= 1) bits = __ldg(a.box + lin3(g, c[0], c[1], c[2]));
             }
+            // one instance of the tap loop (a second one for stencils away from the x seam made
+            // the kernel larger and measured slower)
             float cub[NFM], lin[NFM];
-            if (c[0] >= 1 && c[0] + 2 < g.n0)
-                tap_sums<NFM, true>(a, ox, oy, oz, c[0] - 1, wc, xf, cub, lin);
-            else
-                tap_sums<NFM, false>(a, ox, oy, oz, 0, wc, xf, cub, lin);
+            tap_sums<NFM>(a, ox, oy, oz, wc, xf, cub, lin);
 #pragma unroll
             for (int q = 0; q < NFM; ++q) {
                 if (q >= a.nfields) break;
@@ -448,7 +437,7 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             a.D_next[jj] = make_float4(d[0], d[1], d[2], 0.f);
         }
     }
-    flush_counters(cnt, a.counters);
+    flush_counters_common(cnt, a.counters);
 }
 
 }  // namespace

@@ -346,8 +346,12 @@ template <typename T>
 __device__ __forceinline__ T node_position(T lo, int k, T dx) { return fma_rn_t(T(k), dx, lo); }
 
 // sin(pi d), cos(pi d) of a small offset d from their Taylor series in r = pi d by Horner's rule
-// in u = r^2.  FP64: |d| <= 1/16 (|r| <= 0.2), through r^11 / r^12 (the first neglected term is
-// below 1e-19).  FP32: |d| <= 1/8 (|r| <= 0.4), through r^7 / r^8 (below 1e-9).
+// in u = r^2, with fewer terms for the smallest offsets (the first neglected term relative to the
+// result in brackets):
+//   FP64, |d| <= 1/256 (|r| <= 0.0123): sin through r^7, cos through r^6 [1e-20];
+//   FP64, |d| <= 1/16  (|r| <= 0.2):    sin through r^11, cos through r^12 [1e-19];
+//   FP32, |d| <= 1/256: sin through r^3, cos through r^2 [1e-9];
+//   FP32, |d| <= 1/8   (|r| <= 0.4):    sin through r^7, cos through r^8 [1e-9].
 template <typename T>
 __device__ __forceinline__ T small_offset_limit();
 template <>
@@ -358,23 +362,33 @@ __device__ __forceinline__ float small_offset_limit<float>() { return 0.125f; }
 __device__ __forceinline__ void sincospi_small(double d, double *s, double *c)
 {
     const double r = mul_rn_t(3.141592653589793238462643, d), u = mul_rn_t(r, r);
-    double ps = -1.0 / 39916800.0, pc = 1.0 / 479001600.0;
-    ps = fma_rn_t(u, ps, 1.0 / 362880.0);
-    ps = fma_rn_t(u, ps, -1.0 / 5040.0);
-    ps = fma_rn_t(u, ps, 1.0 / 120.0);
+    double ps, pc;
+    if (fabs(d) <= 1.0 / 256.0) {
+        ps = fma_rn_t(u, -1.0 / 5040.0, 1.0 / 120.0);
+        pc = fma_rn_t(u, -1.0 / 720.0, 1.0 / 24.0);
+    } else {
+        ps = fma_rn_t(u, -1.0 / 39916800.0, 1.0 / 362880.0);
+        pc = fma_rn_t(u, 1.0 / 479001600.0, -1.0 / 3628800.0);
+        ps = fma_rn_t(u, ps, -1.0 / 5040.0);
+        pc = fma_rn_t(u, pc, 1.0 / 40320.0);
+        ps = fma_rn_t(u, ps, 1.0 / 120.0);
+        pc = fma_rn_t(u, pc, -1.0 / 720.0);
+        pc = fma_rn_t(u, pc, 1.0 / 24.0);
+    }
     ps = fma_rn_t(u, ps, -1.0 / 6.0);
-    ps = fma_rn_t(u, ps, 1.0);
-    pc = fma_rn_t(u, pc, -1.0 / 3628800.0);
-    pc = fma_rn_t(u, pc, 1.0 / 40320.0);
-    pc = fma_rn_t(u, pc, -1.0 / 720.0);
-    pc = fma_rn_t(u, pc, 1.0 / 24.0);
     pc = fma_rn_t(u, pc, -0.5);
+    ps = fma_rn_t(u, ps, 1.0);
     *s = mul_rn_t(r, ps);
     *c = fma_rn_t(u, pc, 1.0);
 }
 __device__ __forceinline__ void sincospi_small(float d, float *s, float *c)
 {
     const float r = mul_rn_t(3.14159265358979f, d), u = mul_rn_t(r, r);
+    if (fabsf(d) <= 1.f / 256.f) {
+        *s = mul_rn_t(r, fma_rn_t(u, -1.f / 6.f, 1.f));
+        *c = fma_rn_t(u, -0.5f, 1.f);
+        return;
+    }
     float ps = fma_rn_t(u, -1.f / 5040.f, 1.f / 120.f), pc = fma_rn_t(u, 1.f / 40320.f, -1.f / 720.f);
     ps = fma_rn_t(u, ps, -1.f / 6.f);
     ps = fma_rn_t(u, ps, 1.f);
@@ -764,6 +778,46 @@ __device__ __forceinline__ void flush_counters(const LocalCounters &c, DevCounte
                                        &g->tiles_fallback};
         for (int q = 0; q < 13; ++q) {
             if (q == 5 || q == 7) {
+                if (s[q]) atomicMax(dst[q], s[q]);
+            } else if (s[q]) {
+                atomicAdd(dst[q], s[q]);
+            }
+        }
+    }
+}
+
+// flush_counters for blocks whose threads hold one target each: where no thread of the block met a
+// failure, an FP64 re-solve, a quintic order or a fallback (one barrier decides, for the whole
+// block), only the seven counters that can be nonzero are reduced.  Called by every thread.
+__device__ __forceinline__ void flush_counters_common(const LocalCounters &c, DevCounters *g)
+{
+    if (g == nullptr) return;
+    const unsigned rare = c.fl | c.fn | c.ff | c.f64 | c.oh2 | c.fallback;
+    if (__syncthreads_or(rare != 0u)) {
+        flush_counters(c, g);
+        return;
+    }
+    __shared__ unsigned long long s[7];
+    if (threadIdx.x < 7) s[threadIdx.x] = 0ull;
+    __syncthreads();
+    const unsigned v[7] = {warp_sum(c.targets), warp_sum(c.hops), warp_max(c.hops_max), warp_sum(c.iters),
+                           warp_max(c.iters_max), warp_sum(c.oh0), warp_sum(c.oh1)};
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            if (q == 2 || q == 4)
+                atomicMax(&s[q], (unsigned long long)v[q]);
+            else if (v[q])
+                atomicAdd(&s[q], (unsigned long long)v[q]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *dst[7] = {&g->targets, &g->hops_sum, &g->hops_max, &g->iters_sum, &g->iters_max,
+                                      &g->order_hist[0], &g->order_hist[1]};
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            if (q == 2 || q == 4) {
                 if (s[q]) atomicMax(dst[q], s[q]);
             } else if (s[q]) {
                 atomicAdd(dst[q], s[q]);
