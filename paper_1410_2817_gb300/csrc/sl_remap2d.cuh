@@ -376,7 +376,7 @@ __device__ __noinline__ TargetOut slow_target2(const TileArgs &a, const Win2 w, 
 }
 
 // ---- the flag pass: planar staging -> float4 records with the flag bits -------------------------
-// Sec. 2.3 jump test from the two one-sided differences dp = h+ - h, dm = h - h+ of a node.
+// Sec. 2.3 jump test from the two one-sided differences dp = h+ - h, dm = h - h- of a node.
 __device__ __forceinline__ bool jump_dd(float dp, float dm, float thr)
 {
     return fabsf(dp - dm) > thr * fmaxf(fabsf(dp), fabsf(dm));

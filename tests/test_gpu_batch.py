@@ -192,6 +192,9 @@ def test_batch_rejects_ineligible_grids(sl):
     assert sl.sl_batch_workspace_bytes([g64]) == 0
     g3d = sl.Grid(3, (16, 16, 16), 2, sl.SL_F32)
     assert sl.sl_batch_workspace_bytes([g3d]) == 0
+    # the tile bodies invert in FP32: a grid that asks for FP64 inversion of every target is not batched
+    gn = sl.Grid(2, (32, 32), 2, sl.SL_F32, newton_mode=sl.SL_NEWTON_F64)
+    assert sl.sl_batch_workspace_bytes([gn]) == 0
     a = sl.Grid(2, (32, 32), 2, sl.SL_F32)
     c = sl.Grid(2, (32, 32), 3, sl.SL_F32)
     f = [torch.zeros((2, 32, 32), device=DEV), torch.zeros((3, 32, 32), device=DEV)]
