@@ -461,8 +461,8 @@ __device__ __forceinline__ int target_y(int y0, int k) { return y0 + (int)(threa
 // start points of tile t's targets from the displacements in registers, into slot S (float2 per
 // target, index (2 k + h) NT + thread); their box
 template <class Cfg>
-__device__ __forceinline__ void start_points2(const TileArgs &a, int x0, int y0, const float2 *dj, float2 *S, int &mnx,
-                                              int &mny, int &mxx, int &mxy)
+__device__ __forceinline__ void start_points2(const TileArgs &a, int x0, int y0, int ylim, const float2 *dj, float2 *S,
+                                              int &mnx, int &mny, int &mxx, int &mxy)
 {
     mnx = mny = INT_MAX;
     mxx = mxy = INT_MIN;
@@ -472,7 +472,7 @@ __device__ __forceinline__ void start_points2(const TileArgs &a, int x0, int y0,
         for (int h = 0; h < 2; ++h) {
             const int jx = target_x<Cfg>(x0, h), jy = target_y<Cfg>(y0, k);
             float2 s = make_float2((float)jx, (float)jy);
-            if (jx < a.n0 && jy < a.n1) {
+            if (jx < a.n0 && jy < ylim) {
                 s = start_point(jx, jy, dj[2 * k + h]);
                 mnx = min(mnx, (int)floorf(s.x));
                 mny = min(mny, (int)floorf(s.y));
@@ -486,14 +486,14 @@ __device__ __forceinline__ void start_points2(const TileArgs &a, int x0, int y0,
 
 // displacements of tile t's targets into registers
 template <class Cfg>
-__device__ __forceinline__ void load_dj(const TileArgs &a, int x0, int y0, float2 *dj)
+__device__ __forceinline__ void load_dj(const TileArgs &a, int x0, int y0, int ylim, float2 *dj)
 {
 #pragma unroll
     for (int k = 0; k < Cfg::PPT; ++k) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int jx = target_x<Cfg>(x0, h), jy = target_y<Cfg>(y0, k);
-            dj[2 * k + h] = (jx < a.n0 && jy < a.n1)
+            dj[2 * k + h] = (jx < a.n0 && jy < ylim)
                                 ? __ldg(reinterpret_cast<const float2 *>(a.D) + ((long long)jy * a.n0 + jx))
                                 : make_float2(0.f, 0.f);
         }
@@ -595,8 +595,8 @@ __device__ __forceinline__ bool fast_target(const Win2 &w, int base, const float
 
 // Phase 4 of one tile: every target of the thread; general-path targets after the loop.
 template <class Cfg, int NF>
-__device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0, const Win2 &w, const float2 *sD,
-                                              const float4 *sR, const float2 *S, LocalCounters &cnt)
+__device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0, int ylim, const Win2 &w,
+                                              const float2 *sD, const float4 *sR, const float2 *S, LocalCounters &cnt)
 {
     const bool limit = a.max_order >= 1 && a.thr >= 0.f;
     const bool lin_only = a.max_order == 0;
@@ -613,7 +613,7 @@ __device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0,
         unsigned na = 0u, nb = 0u;
         const bool oka = fast_target<Cfg, NF>(w, base, sD, sR, jxa, jy, sa, limit, lin_only, va, na);
         const bool okb = fast_target<Cfg, NF>(w, base, sD, sR, jxb, jy, sb, limit, lin_only, vb, nb);
-        const bool ina = jxa < a.n0 && jy < a.n1, inb = jxb < a.n0 && jy < a.n1;
+        const bool ina = jxa < a.n0 && jy < ylim, inb = jxb < a.n0 && jy < ylim;
         const bool fa = ina && oka && w.mode != 0, fb = inb && okb && w.mode != 0;
         const long long jj = (long long)jy * a.n0 + jxa;
         const int hb = Cfg::PX;  // the second target is PX columns to the right
@@ -663,17 +663,52 @@ __device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0,
 // eq. (vel): the next step's trajectories of the tile's own nodes (fused steps; the velocity is
 // given, so they do not depend on the fields being remapped)
 template <class Cfg>
-__device__ __forceinline__ void integrate_next2(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0)
+__device__ __forceinline__ void integrate_next2(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0, int ylim)
 {
 #pragma unroll 1
     for (int q = 0; q < 2 * Cfg::PPT; ++q) {
         const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
-        if (jx >= a.n0 || jy >= a.n1) continue;
+        if (jx >= a.n0 || jy >= ylim) continue;
         float X[3] = {node_position(vn.lo[0], jx, vn.dx[0]), node_position(vn.lo[1], jy, vn.dx[1]), 0.f}, d[3];
         trajectory_cells<float, 2>(vn, X, d);
         reinterpret_cast<float2 *>(a.D_next)[(long long)jy * a.n0 + jx] = make_float2(d[0], d[1]);
     }
 }
+
+// The i-th work item of CTA b: the tile's target columns x0 .. x0 + TX - 1 and rows y0 .. ylim - 1
+// (ylim <= y0: no item).  Items 0 .. R-1 are the tiles b, b + G, .. (R = ntiles / G full rounds).
+// The last, partial round's rem tiles are cut into 2 rem half tiles (the two row passes of a tile)
+// for the CTAs 0 .. 2 rem - 1 when there are enough CTAs, so that no CTA has a whole extra tile.
+struct Item2 {
+    int x0, y0, ylim;
+};
+template <class Cfg>
+__device__ __forceinline__ Item2 item2(const R2Args &A, int b, int i)
+{
+    const int G = (int)gridDim.x, R = A.ntiles / G, rem = A.ntiles - R * G;
+    const bool split = Cfg::PPT == 2 && rem > 0 && 2 * rem <= G;
+    Item2 it = {0, 0, 0};
+    int t = -1, half = -1;
+    if (i < R)
+        t = b + i * G;
+    else if (i == R && split && b < 2 * rem)
+        t = R * G + (b >> 1), half = b & 1;
+    else if (i == R && !split && b < rem)
+        t = R * G + b;
+    if (t < 0) return it;
+    const int tr = t / A.tiles_x;
+    it.x0 = (t - tr * A.tiles_x) * Cfg::TX;
+    it.y0 = tr * Cfg::TY;
+    it.ylim = min(A.t.n1, it.y0 + Cfg::TY);
+    if (half >= 0) {
+        // rows y0 + half ROWS .. : target_y gives the first pass exactly these rows, the second
+        // pass rows at or beyond ylim
+        it.y0 += half * Cfg::ROWS;
+        it.ylim = min(A.t.n1, it.y0 + Cfg::ROWS);
+    }
+    return it;
+}
+__device__ __forceinline__ bool item_valid(const Item2 &it) { return it.ylim > it.y0; }
 
 template <class Cfg, int NF, bool FUSED>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
@@ -706,34 +741,32 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
     }
     __syncthreads();
     unsigned phase = 0u;  // bit p: parity of slot p's next phase
-    int t = blockIdx.x;
+    const int b = (int)blockIdx.x;
+    Item2 cur = item2<Cfg>(A, b, 0);
     float2 dj[2 * PPT];
-    if (t < A.ntiles) {
-        // prologue: start points and window of the first tile, displacements of the second
-        const int tr = t / A.tiles_x;
-        load_dj<Cfg>(a, (t - tr * A.tiles_x) * TX, tr * TY, dj);
+    if (item_valid(cur)) {
+        // prologue: start points and window of the first item, displacements of the second
+        load_dj<Cfg>(a, cur.x0, cur.y0, cur.ylim, dj);
         int mnx, mny, mxx, mxy;
-        start_points2<Cfg>(a, (t - tr * A.tiles_x) * TX, tr * TY, dj, spts, mnx, mny, mxx, mxy);
+        start_points2<Cfg>(a, cur.x0, cur.y0, cur.ylim, dj, spts, mnx, mny, mxx, mxy);
         reduce_window<Cfg>(A, mnx, mny, mxx, mxy, box, W, 0);
         __syncthreads();
         stage_window2<Cfg, NF>(A, maps, W[0], stage, dwin, &bar[0]);
         __syncthreads();
         mbar_finish(W[0], &bar[0]);
-        if (t + G < A.ntiles) {
-            const int t2 = t + G, tr2 = t2 / A.tiles_x;
-            load_dj<Cfg>(a, (t2 - tr2 * A.tiles_x) * TX, tr2 * TY, dj);
-        }
+        const Item2 n1 = item2<Cfg>(A, b, 1);
+        if (item_valid(n1)) load_dj<Cfg>(a, n1.x0, n1.y0, n1.ylim, dj);
     }
-    for (int k = 0; t < A.ntiles; ++k, t += G) {
+    for (int k = 0; item_valid(cur); ++k) {
         const int p = k & 1;
-        const int tr = t / A.tiles_x, x0 = (t - tr * A.tiles_x) * TX, y0 = tr * TY;
-        const int tn = t + G;
-        // start points of the next tile (its displacements are in registers) into the box
-        if (tn < A.ntiles) {
-            const int trn = tn / A.tiles_x;
+        const int x0 = cur.x0, y0 = cur.y0, ylim = cur.ylim;
+        const Item2 nx = item2<Cfg>(A, b, k + 1);
+        const bool has_next = item_valid(nx);
+        // start points of the next item (its displacements are in registers) into the box
+        if (has_next) {
             int mnx, mny, mxx, mxy;
-            start_points2<Cfg>(a, (tn - trn * A.tiles_x) * TX, trn * TY, dj, spts + (p ^ 1) * 2 * PPT * Cfg::NT, mnx, mny,
-                               mxx, mxy);
+            start_points2<Cfg>(a, nx.x0, nx.y0, nx.ylim, dj, spts + (p ^ 1) * 2 * PPT * Cfg::NT, mnx, mny, mxx,
+                               mxy);
             mnx = __reduce_min_sync(0xffffffffu, mnx);
             mny = __reduce_min_sync(0xffffffffu, mny);
             mxx = __reduce_max_sync(0xffffffffu, mxx);
@@ -756,7 +789,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
         // before its own reads
         (void)mbar_test(&bar[p], (phase >> p) & 1u);
         phase ^= 1u << p;
-        if (threadIdx.x == 0 && tn < A.ntiles) {
+        if (threadIdx.x == 0 && has_next) {
             W[p ^ 1] = window2<Cfg>(box[0], box[1], box[2], box[3], a.n0, a.n1, A.use_tma != 0);
             box[0] = box[1] = INT_MAX;
             box[2] = box[3] = INT_MIN;
@@ -765,18 +798,17 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
         if (w.mode != 0) flag_pass<Cfg, NF>(w, stage, rec, a.thr, a.max_order >= 1 && a.thr >= 0.f);
         fence_proxy_async();  // the staging planes' reads before the next box copies overwrite them
         __syncthreads();
-        // the staging planes are free: copy the next tile's window while this one is computed
-        if (tn < A.ntiles) {
+        // the staging planes are free: copy the next item's window while this one is computed
+        if (has_next) {
             stage_window2<Cfg, NF>(A, maps, W[p ^ 1], stage, dwin + (p ^ 1) * WX * WY, &bar[p ^ 1]);
-            if (tn + G < A.ntiles) {
-                const int t2 = tn + G, tr2 = t2 / A.tiles_x;
-                load_dj<Cfg>(a, (t2 - tr2 * A.tiles_x) * TX, tr2 * TY, dj);
-            }
+            const Item2 n2 = item2<Cfg>(A, b, k + 2);
+            if (item_valid(n2)) load_dj<Cfg>(a, n2.x0, n2.y0, n2.ylim, dj);
         }
-        if (FUSED && a.D_next != nullptr) integrate_next2<Cfg>(a, vn, x0, y0);
-        compute_tile2<Cfg, NF>(a, x0, y0, w, dwin + p * WX * WY, rec, spts + p * 2 * PPT * Cfg::NT, cnt);
+        if (FUSED && a.D_next != nullptr) integrate_next2<Cfg>(a, vn, x0, y0, ylim);
+        compute_tile2<Cfg, NF>(a, x0, y0, ylim, w, dwin + p * WX * WY, rec, spts + p * 2 * PPT * Cfg::NT, cnt);
         __syncthreads();
-        if (tn < A.ntiles) mbar_finish(W[p ^ 1], &bar[p ^ 1]);
+        if (has_next) mbar_finish(W[p ^ 1], &bar[p ^ 1]);
+        cur = nx;
     }
     flush_counters(cnt, a.counters);
 }
