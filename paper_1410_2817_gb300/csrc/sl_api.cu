@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "sl_internal.h"
 
 static thread_local char g_last_error[512];
@@ -112,7 +114,7 @@ static const char *check_desc(const sl_grid_desc *d)
 }
 
 struct Layout {
-    size_t counters, partials, moment_out, flags, flags2, D0, D1, rk, total;
+    size_t counters, stripes, partials, moment_out, flags, flags2, D0, D1, rk, total;
 };
 
 static Layout layout_of(const sl_grid_desc *d)
@@ -125,6 +127,8 @@ static Layout layout_of(const sl_grid_desc *d)
     size_t off = 0;
     L.counters = off;
     off += align256(sizeof(DevCounters));
+    L.stripes = off;
+    off += align256(sizeof(DevCounters) * SL_COUNTER_STRIPES);
     L.partials = off;
     off += align256(sizeof(double) * 8 * SL_MOMENT_BLOCKS);
     L.moment_out = off;
@@ -185,6 +189,7 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     g->ws = (char *)dev_workspace;
     g->ws_bytes = ws_bytes;
     g->counters = (DevCounters *)(g->ws + L.counters);
+    g->stripes = (DevCounters *)(g->ws + L.stripes);
     g->partials = (double *)(g->ws + L.partials);
     g->moment_out = (double *)(g->ws + L.moment_out);
     g->flags = (uint8_t *)(g->ws + L.flags);
@@ -314,10 +319,28 @@ extern "C" sl_status sl_remap_fields_debug(sl_grid *g, const void *const *in, vo
     return remap_entry(g, in, out, dbg, stream);
 }
 
+// the grid's counters: the main copy and the per-SM stripes, summed (maxima for the two maxima)
 static sl_status read_counters(sl_grid *g, DevCounters *c, cudaStream_t s)
 {
+    static thread_local DevCounters st[SL_COUNTER_STRIPES];
     SL_CUDA(cudaMemcpyAsync(c, g->counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, s), "read counters");
+    SL_CUDA(cudaMemcpyAsync(st, g->stripes, sizeof(st), cudaMemcpyDeviceToHost, s), "read counters");
     SL_CUDA(cudaStreamSynchronize(s), "read counters");
+    for (int k = 0; k < SL_COUNTER_STRIPES; ++k) {
+        const DevCounters &d = st[k];
+        c->targets += d.targets;
+        c->fail_locate += d.fail_locate;
+        c->fail_newton += d.fail_newton;
+        c->fail_fold += d.fail_fold;
+        c->hops_sum += d.hops_sum;
+        c->hops_max = std::max(c->hops_max, d.hops_max);
+        c->iters_sum += d.iters_sum;
+        c->iters_max = std::max(c->iters_max, d.iters_max);
+        c->newton_f64 += d.newton_f64;
+        for (int q = 0; q < 3; ++q) c->order_hist[q] += d.order_hist[q];
+        c->tiles_fallback += d.tiles_fallback;
+        c->timeouts += d.timeouts;
+    }
     return SL_OK;
 }
 
@@ -622,6 +645,8 @@ extern "C" sl_status sl_reset_diagnostics(sl_grid *g, void *stream)
 {
     if (!g) return fail_arg("grid is NULL");
     SL_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(DevCounters), (cudaStream_t)stream), "sl_reset_diagnostics");
+    SL_CUDA(cudaMemsetAsync(g->stripes, 0, sizeof(DevCounters) * SL_COUNTER_STRIPES, (cudaStream_t)stream),
+            "sl_reset_diagnostics");
     return SL_OK;
 }
 

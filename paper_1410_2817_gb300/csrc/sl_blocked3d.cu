@@ -437,7 +437,9 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
             a.D_next[jj] = make_float4(d[0], d[1], d[2], 0.f);
         }
     }
-    flush_counters_common(cnt, a.counters);
+    unsigned smid;
+    asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    flush_counters_warp(cnt, a.counters + (smid % SL_COUNTER_STRIPES));
 }
 
 }  // namespace
@@ -503,7 +505,7 @@ cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, cons
         a.f.in[q] = (const float *)in[q];
         a.f.out[q] = (float *)out[q];
     }
-    a.counters = g->counters;
+    a.counters = g->stripes;  // one copy per SM: a 256-target CTA adds its counters into its SM's
     dim3 grid((unsigned)((g->n[0] + BX - 1) / BX), (unsigned)((g->n[1] + BY - 1) / BY),
               (unsigned)((g->n[2] + BZ - 1) / BZ));
     VelArgs<float> vn;

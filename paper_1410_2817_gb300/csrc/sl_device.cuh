@@ -786,42 +786,40 @@ __device__ __forceinline__ void flush_counters(const LocalCounters &c, DevCounte
     }
 }
 
-// flush_counters for blocks whose threads hold one target each: where no thread of the block met a
-// failure, an FP64 re-solve, a quintic order or a fallback (one barrier decides, for the whole
-// block), only the seven counters that can be nonzero are reduced.  Called by every thread.
-__device__ __forceinline__ void flush_counters_common(const LocalCounters &c, DevCounters *g)
+// Per-warp flush with no block barrier, for kernels whose threads hold one target each and whose
+// counters are per-SM copies (so that few CTAs add into one copy): the warp's sums and maxima go
+// straight to global memory from lane 0, the rare counters only where the warp met one.
+__device__ __forceinline__ void flush_counters_warp(const LocalCounters &c, DevCounters *g)
 {
     if (g == nullptr) return;
-    const unsigned rare = c.fl | c.fn | c.ff | c.f64 | c.oh2 | c.fallback;
-    if (__syncthreads_or(rare != 0u)) {
-        flush_counters(c, g);
-        return;
-    }
-    __shared__ unsigned long long s[7];
-    if (threadIdx.x < 7) s[threadIdx.x] = 0ull;
-    __syncthreads();
     const unsigned v[7] = {warp_sum(c.targets), warp_sum(c.hops), warp_max(c.hops_max), warp_sum(c.iters),
                            warp_max(c.iters_max), warp_sum(c.oh0), warp_sum(c.oh1)};
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            if (q == 2 || q == 4)
-                atomicMax(&s[q], (unsigned long long)v[q]);
-            else if (v[q])
-                atomicAdd(&s[q], (unsigned long long)v[q]);
-        }
+    const unsigned rare = c.fl | c.fn | c.ff | c.f64 | c.oh2 | c.fallback;
+    const bool any_rare = __any_sync(0xffffffffu, rare != 0u);
+    unsigned r[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    if (any_rare) {
+        r[0] = warp_sum(c.fl);
+        r[1] = warp_sum(c.fn);
+        r[2] = warp_sum(c.ff);
+        r[3] = warp_sum(c.f64);
+        r[4] = warp_sum(c.oh2);
+        r[5] = warp_sum(c.fallback);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long *dst[7] = {&g->targets, &g->hops_sum, &g->hops_max, &g->iters_sum, &g->iters_max,
-                                      &g->order_hist[0], &g->order_hist[1]};
+    if ((threadIdx.x & 31) == 0) {
+        if (v[0]) atomicAdd(&g->targets, (unsigned long long)v[0]);
+        if (v[1]) atomicAdd(&g->hops_sum, (unsigned long long)v[1]);
+        if (v[2]) atomicMax(&g->hops_max, (unsigned long long)v[2]);
+        if (v[3]) atomicAdd(&g->iters_sum, (unsigned long long)v[3]);
+        if (v[4]) atomicMax(&g->iters_max, (unsigned long long)v[4]);
+        if (v[5]) atomicAdd(&g->order_hist[0], (unsigned long long)v[5]);
+        if (v[6]) atomicAdd(&g->order_hist[1], (unsigned long long)v[6]);
+        if (any_rare) {
+            unsigned long long *dst[6] = {&g->fail_locate, &g->fail_newton, &g->fail_fold, &g->newton_f64,
+                                          &g->order_hist[2], &g->tiles_fallback};
 #pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            if (q == 2 || q == 4) {
-                if (s[q]) atomicMax(dst[q], s[q]);
-            } else if (s[q]) {
-                atomicAdd(dst[q], s[q]);
-            }
+            for (int q = 0; q < 6; ++q)
+                if (r[q]) atomicAdd(dst[q], (unsigned long long)r[q]);
         }
     }
 }
+

@@ -17,6 +17,8 @@ struct sl_grid {
     char *ws;
     size_t ws_bytes;
     DevCounters *counters;
+    DevCounters *stripes;        // SL_COUNTER_STRIPES more copies, one per SM (kernels with many small
+                                 // CTAs add into their SM's copy); read together with counters
     double *partials;            // moments: SL_MOMENT_BLOCKS x 8
     double *moment_out;          // 8 doubles
     uint8_t *flags;              // N
@@ -45,6 +47,7 @@ struct sl_grid {
 };
 
 #define SL_MOMENT_BLOCKS 512
+#define SL_COUNTER_STRIPES 256
 
 // precision-dispatched launchers (sl_kernels.cu)
 template <typename T>
