@@ -786,9 +786,10 @@ __device__ __forceinline__ void flush_counters(const LocalCounters &c, DevCounte
     }
 }
 
-// Per-warp flush with no block barrier, for kernels whose threads hold one target each and whose
-// counters are per-SM copies (so that few CTAs add into one copy): the warp's sums and maxima go
-// straight to global memory from lane 0, the rare counters only where the warp met one.
+// Per-warp flush with no block barrier (a barrier at the end of a block costs its early warps the
+// wait for its slowest target): the warp's sums and maxima go straight to global memory from lane
+// 0, the rare counters only where the warp met one.  For kernels whose counters see few concurrent
+// adders (the blocked 3-D kernel adds into per-SM copies).
 __device__ __forceinline__ void flush_counters_warp(const LocalCounters &c, DevCounters *g)
 {
     if (g == nullptr) return;
