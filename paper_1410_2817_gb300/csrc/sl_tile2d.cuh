@@ -56,6 +56,7 @@ struct TileArgs {
     const float *in[SL_MAX_FIELDS];
     float *out[SL_MAX_FIELDS];
     DevCounters *counters;
+    DevCounters *stripes;  // the grid's per-SM copies of the counters (single grids; null in batches)
     // carried velocity (Sec. 3.2): D_next = dt u / dx from the remapped fields vf[0], vf[1]
     int carried, vf[2];
     float csc[2];
@@ -729,6 +730,18 @@ __device__ __forceinline__ void process_tile(const TileArgs &a, const VelArgs<fl
     if (FUSED && a.D_next != nullptr && a.carried) carried_next<Cfg>(a, x0, y0);
 }
 
+// the counters of a one-tile CTA: each warp adds into its SM's copy, with no block barrier
+__device__ __forceinline__ void flush_counters_sm(const LocalCounters &cnt, const TileArgs &a)
+{
+    if (a.stripes == nullptr) {
+        flush_counters(cnt, a.counters);
+        return;
+    }
+    unsigned smid;
+    asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    flush_counters_warp(cnt, a.stripes + (smid % SL_COUNTER_STRIPES));
+}
+
 template <class Cfg, int NF, bool FUSED>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const __grid_constant__ TileArgs a, const VelArgs<float> vn)
 {
@@ -738,7 +751,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB) remap_tiled2d_kernel(const
     LocalCounters cnt;
     cnt.clear();
     process_tile<Cfg, NF, FUSED>(a, vn, blockIdx.x * Cfg::TX, blockIdx.y * Cfg::TY, sm, sBox, cnt);
-    flush_counters(cnt, a.counters);
+    flush_counters_sm(cnt, a);
 }
 
 // Pipelined persistent variant: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... and
@@ -870,6 +883,7 @@ __host__ inline TileArgs make_tile_args(const sl_grid *g, const void *D, void *D
         a.out[f] = (float *)out[f];
     }
     a.counters = g->counters;
+    a.stripes = g->stripes;
     return a;
 }
 

@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(CfgZ::NT, CfgZ::MINB)
     LocalCounters cnt;
     cnt.clear();
     process_tile_z2<NF, FUSED>(a, vn, blockIdx.x * CfgZ::TX, blockIdx.y * CfgZ::TY, sm, sBox, cnt);
-    flush_counters(cnt, a.counters);
+    flush_counters_sm(cnt, a);
 }
 
 template <int NF, bool FUSED>
