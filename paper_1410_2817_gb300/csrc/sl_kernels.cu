@@ -429,7 +429,10 @@ __global__ void __launch_bounds__(256)
             f.out[q][jj] = sum;
         }
     }
-    flush_counters(cnt, counters);
+    // each warp adds into its SM's copy of the counters (the launch passes the per-SM copies)
+    unsigned smid;
+    asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    flush_counters_warp(cnt, counters + (smid % SL_COUNTER_STRIPES));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -596,18 +599,18 @@ cudaError_t Launch<T>::remap_generic(const sl_grid *g, const void *D, const uint
     const int nmode = sizeof(T) == 8 ? 0 : (g->desc.newton_mode == SL_NEWTON_F64 ? 1 : 2);
     if (g->dim == 2) {
         if (nmode == 0)
-            remap_generic_kernel<T, 2, 0><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->counters);
+            remap_generic_kernel<T, 2, 0><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->stripes);
         else if (nmode == 1)
-            remap_generic_kernel<T, 2, 1><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->counters);
+            remap_generic_kernel<T, 2, 1><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->stripes);
         else
-            remap_generic_kernel<T, 2, 2><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->counters);
+            remap_generic_kernel<T, 2, 2><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->stripes);
     } else {
         if (nmode == 0)
-            remap_generic_kernel<T, 3, 0><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->counters);
+            remap_generic_kernel<T, 3, 0><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->stripes);
         else if (nmode == 1)
-            remap_generic_kernel<T, 3, 1><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->counters);
+            remap_generic_kernel<T, 3, 1><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->stripes);
         else
-            remap_generic_kernel<T, 3, 2><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->counters);
+            remap_generic_kernel<T, 3, 2><<<blocks, 256, 0, s>>>(ga, (const T *)D, g->ds, flags, f, d, g->stripes);
     }
     return cudaGetLastError();
 }
