@@ -164,16 +164,22 @@ __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sin
 // series of sin(pi r) through r^9 and of cos(pi r) through r^10 (truncation below 2e-9 for
 // |pi r| <= pi/4) by Horner's rule in r^2, then the quadrant q mod 4.  Integers and half-integers
 // give exact zeros (stagnation lines stay at rest).  Valid for |x| < 2^30.
+// (-1)^k pi^(2k+1) / (2k+1)!, k = 4 .. 0, and (-1)^k pi^(2k) / (2k)!, k = 5 .. 1
+struct SinPiF32 {
+    static constexpr float s4 = 8.214588661e-2f, s3 = -5.992645293e-1f, s2 = 2.550164040e+0f, s1 = -5.167712780e+0f,
+                           s0 = 3.141592654e+0f;
+    static constexpr float c5 = -2.580689139e-2f, c4 = 2.353306304e-1f, c3 = -1.335262769e+0f, c2 = 4.058712126e+0f,
+                           c1 = -4.934802201e+0f;
+};
+
 __device__ __forceinline__ void sincospi_t(float x, float *s, float *c)
 {
     const float q = rintf(2.f * x);
     const float r = fmaf(-0.5f, q, x);
     const float u = r * r;
-    // (-1)^k pi^(2k+1) / (2k+1)!  and  (-1)^k pi^(2k) / (2k)!
-    float sn = r * fmaf(u, fmaf(u, fmaf(u, fmaf(u, 8.214588661e-2f, -5.992645293e-1f), 2.550164040e+0f),
-                                -5.167712780e+0f), 3.141592654e+0f);
-    float cs = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, -2.580689139e-2f, 2.353306304e-1f), -1.335262769e+0f),
-                                4.058712126e+0f), -4.934802201e+0f), 1.f);
+    typedef SinPiF32 K;
+    float sn = r * fmaf(u, fmaf(u, fmaf(u, fmaf(u, K::s4, K::s3), K::s2), K::s1), K::s0);
+    float cs = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, K::c5, K::c4), K::c3), K::c2), K::c1), 1.f);
     const int qi = (int)q;
     if (qi & 1) {
         const float t = sn;
@@ -464,6 +470,120 @@ __device__ __forceinline__ void rk4_trig_cells(const VelArgs<T> &v, const T X[3]
         const T sum = fma_rn_t(T(2), k3[a], fma_rn_t(T(2), k2[a], k1[a])) + k4[a];
         out[a] = mul_rn_t(mul_rn_t(h6, sum), v.inv_dx[a]);
     }
+}
+
+// ---- the swirl's RK4 step for two nodes at once -------------------------------------------------
+// The operations of rk4_trig_cells<float, 2> lane by lane on packed FP32x2 instructions (each lane
+// of __ffma2_rn / __fmul2_rn rounds as fmaf / __fmul_rn do, so that every node gets the bits the
+// scalar code gives it); where the two nodes' stage offsets need different series, each lane takes
+// the scalar path.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void quadrant_fix(int qi, float &sn, float &cs)
+{
+    if (qi & 1) {
+        const float t = sn;
+        sn = cs;
+        cs = -t;
+    }
+    if (qi & 2) {
+        sn = -sn;
+        cs = -cs;
+    }
+}
+
+__device__ __forceinline__ void sincospi_pair(float2 x, float2 *s, float2 *c)
+{
+    typedef SinPiF32 K;
+    const float2 q = make_float2(rintf(2.f * x.x), rintf(2.f * x.y));
+    const float2 r = __ffma2_rn(f2(-0.5f), q, x);
+    const float2 u = __fmul2_rn(r, r);
+    float2 ps = __ffma2_rn(u, f2(K::s4), f2(K::s3));
+    ps = __ffma2_rn(u, ps, f2(K::s2));
+    ps = __ffma2_rn(u, ps, f2(K::s1));
+    ps = __ffma2_rn(u, ps, f2(K::s0));
+    float2 pc = __ffma2_rn(u, f2(K::c5), f2(K::c4));
+    pc = __ffma2_rn(u, pc, f2(K::c3));
+    pc = __ffma2_rn(u, pc, f2(K::c2));
+    pc = __ffma2_rn(u, pc, f2(K::c1));
+    pc = __ffma2_rn(u, pc, f2(1.f));
+    float2 sn = __fmul2_rn(r, ps), cs = pc;
+    quadrant_fix((int)q.x, sn.x, cs.x);
+    quadrant_fix((int)q.y, sn.y, cs.y);
+    *s = sn;
+    *c = cs;
+}
+
+// which series sincospi_near takes for the offset d: 0 the short one, 1 the long one, 2 none
+__device__ __forceinline__ int offset_tier(float d)
+{
+    const float a = fabsf(d);
+    return a <= 1.f / 256.f ? 0 : (a <= small_offset_limit<float>() ? 1 : 2);
+}
+
+// sincospi_near for two nodes: (sx, cx) of the base positions x, offsets d = h k
+__device__ __forceinline__ void sincospi_near_pair(float2 sx, float2 cx, float2 x, float h, float2 k, float2 *s,
+                                                   float2 *c)
+{
+    const float2 d = __fmul2_rn(f2(h), k);
+    const int ta = offset_tier(d.x), tb = offset_tier(d.y);
+    if (ta != tb || ta == 2) {
+        sincospi_near(sx.x, cx.x, x.x, h, k.x, &s->x, &c->x);
+        sincospi_near(sx.y, cx.y, x.y, h, k.y, &s->y, &c->y);
+        return;
+    }
+    const float2 r = __fmul2_rn(f2(3.14159265358979f), d), u = __fmul2_rn(r, r);
+    float2 sd, cd;
+    if (ta == 0) {
+        sd = __fmul2_rn(r, __ffma2_rn(u, f2(-1.f / 6.f), f2(1.f)));
+        cd = __ffma2_rn(u, f2(-0.5f), f2(1.f));
+    } else {
+        float2 ps = __ffma2_rn(u, f2(-1.f / 5040.f), f2(1.f / 120.f));
+        float2 pc = __ffma2_rn(u, f2(1.f / 40320.f), f2(-1.f / 720.f));
+        ps = __ffma2_rn(u, ps, f2(-1.f / 6.f));
+        ps = __ffma2_rn(u, ps, f2(1.f));
+        pc = __ffma2_rn(u, pc, f2(1.f / 24.f));
+        pc = __ffma2_rn(u, pc, f2(-0.5f));
+        sd = __fmul2_rn(r, ps);
+        cd = __ffma2_rn(u, pc, f2(1.f));
+    }
+    *s = __ffma2_rn(sx, cd, __fmul2_rn(cx, sd));
+    *c = __ffma2_rn(cx, cd, neg2(__fmul2_rn(sx, sd)));
+}
+
+// trig_velocity<float, 2> of the swirl for two nodes
+__device__ __forceinline__ void swirl_velocity_pair(float2 sX, float2 cX, float2 sY, float2 cY, float ct, float2 &u0,
+                                                    float2 &u1)
+{
+    const float2 s2x = __fmul2_rn(f2(2.f), __fmul2_rn(sX, cX)), s2y = __fmul2_rn(f2(2.f), __fmul2_rn(sY, cY));
+    u0 = __fmul2_rn(__fmul2_rn(__fmul2_rn(sX, sX), s2y), f2(ct));
+    u1 = neg2(__fmul2_rn(__fmul2_rn(__fmul2_rn(sY, sY), s2x), f2(ct)));
+}
+
+// rk4_trig_cells<float, 2> for the swirl at the positions (X.x, Y.x) and (X.y, Y.y): the
+// displacements in cell units, dx of the two nodes in Dx, dy in Dy
+__device__ __forceinline__ void rk4_swirl_pair(const VelArgs<float> &v, float2 X, float2 Y, float2 &Dx, float2 &Dy)
+{
+    const float h = v.dt, hh = 0.5f * v.dt, h6 = v.dt / 6.f;
+    float2 s0x, c0x, s0y, c0y, sx, cx, sy, cy, k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
+    sincospi_pair(X, &s0x, &c0x);
+    sincospi_pair(Y, &s0y, &c0y);
+    swirl_velocity_pair(s0x, c0x, s0y, c0y, v.ct[0], k1x, k1y);
+    sincospi_near_pair(s0x, c0x, X, hh, k1x, &sx, &cx);
+    sincospi_near_pair(s0y, c0y, Y, hh, k1y, &sy, &cy);
+    swirl_velocity_pair(sx, cx, sy, cy, v.ct[1], k2x, k2y);
+    sincospi_near_pair(s0x, c0x, X, hh, k2x, &sx, &cx);
+    sincospi_near_pair(s0y, c0y, Y, hh, k2y, &sy, &cy);
+    swirl_velocity_pair(sx, cx, sy, cy, v.ct[1], k3x, k3y);
+    sincospi_near_pair(s0x, c0x, X, h, k3x, &sx, &cx);
+    sincospi_near_pair(s0y, c0y, Y, h, k3y, &sy, &cy);
+    swirl_velocity_pair(sx, cx, sy, cy, v.ct[2], k4x, k4y);
+    const float2 ax = __ffma2_rn(f2(2.f), k3x, __ffma2_rn(f2(2.f), k2x, k1x));
+    const float2 ay = __ffma2_rn(f2(2.f), k3y, __ffma2_rn(f2(2.f), k2y, k1y));
+    const float2 sumx = make_float2(ax.x + k4x.x, ax.y + k4x.y), sumy = make_float2(ay.x + k4y.x, ay.y + k4y.y);
+    Dx = __fmul2_rn(__fmul2_rn(f2(h6), sumx), f2(v.inv_dx[0]));
+    Dy = __fmul2_rn(__fmul2_rn(f2(h6), sumy), f2(v.inv_dx[1]));
 }
 
 template <typename T, int DIM>

@@ -665,6 +665,24 @@ __device__ __forceinline__ void compute_tile2(const TileArgs &a, int x0, int y0,
 template <class Cfg>
 __device__ __forceinline__ void integrate_next2(const TileArgs &a, const VelArgs<float> &vn, int x0, int y0, int ylim)
 {
+    if (vn.kind == SL_VEL_SWIRL2D && vn.integrator == SL_RK4 && vn.substeps == 1) {
+        // the swirl: a thread's two nodes of a tile row (PX columns apart) on packed FP32x2 arithmetic
+        float2 *Dn = reinterpret_cast<float2 *>(a.D_next);
+#pragma unroll 1
+        for (int k = 0; k < Cfg::PPT; ++k) {
+            const int jxa = target_x<Cfg>(x0, 0), jxb = target_x<Cfg>(x0, 1), jy = target_y<Cfg>(y0, k);
+            const bool ina = jxa < a.n0 && jy < ylim, inb = jxb < a.n0 && jy < ylim;
+            if (!ina && !inb) continue;
+            const float Y = node_position(vn.lo[1], jy, vn.dx[1]);
+            float2 Dx, Dy;
+            rk4_swirl_pair(vn, make_float2(node_position(vn.lo[0], jxa, vn.dx[0]), node_position(vn.lo[0], jxb, vn.dx[0])),
+                           make_float2(Y, Y), Dx, Dy);
+            const long long jj = (long long)jy * a.n0 + jxa;
+            if (ina) Dn[jj] = make_float2(Dx.x, Dy.x);
+            if (inb) Dn[jj + Cfg::PX] = make_float2(Dx.y, Dy.y);
+        }
+        return;
+    }
 #pragma unroll 1
     for (int q = 0; q < 2 * Cfg::PPT; ++q) {
         const int jx = target_x<Cfg>(x0, q & 1), jy = target_y<Cfg>(y0, q >> 1);
