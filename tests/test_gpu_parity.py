@@ -602,6 +602,21 @@ def test_fused_trajectories_equal_the_trajectory_launch(sl, dt):
     assert torch.equal(gt.get_displacement(), gg.get_displacement())
 
 
+@pytest.mark.parametrize("dt", [0.003, 0.03, 0.3])
+def test_fused_3d_trajectories_equal_the_trajectory_launch(sl, dt):
+    """The blocked 3-D launch's next-step trajectories of the deformation flow equal the trajectory
+    launch's bit for bit, for stage offsets in each series range."""
+    n = (24, 20, 16)
+    kw = dict(velocity="deform3d", velocity_params=[3.0], walk_start=sl.SL_START_BACKWARD)
+    gt = sl.Grid(3, n, 2, sl.SL_F32, **kw)
+    gg = sl.Grid(3, n, 2, sl.SL_F32, kernel=sl.SL_KERNEL_GENERIC, **kw)
+    f = torch.tensor(np.asarray(inputs.deform3d_fields(24))[:, :16, :20, :24], dtype=torch.float32, device=DEV)
+    gt.step(f, torch.empty_like(f), 0.4, dt, 1)
+    gg.advect(0.4 + dt, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(gt.get_displacement(), gg.get_displacement())
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_step_out_equals_step(sl, dtype):
     """sl_step_out (out of place) computes what sl_step computes in place, for odd and even step
