@@ -238,7 +238,7 @@ struct Blocked3Args {
     float4 *D_next;
     const uint8_t *box;   // OR of the flags over each element's 4x4x4 stencil
     Fields3 f;
-    DevCounters *counters;
+    DevCounters *counters;  // the grid's SL_COUNTER_STRIPES per-SM copies of its counters
 };
 
 // eq. (multiZ) in 3-D for up to NFM fields: the 4x4x4 cubic (Z~1) sums and the trilinear (Z~0)
@@ -505,7 +505,7 @@ cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, cons
         a.f.in[q] = (const float *)in[q];
         a.f.out[q] = (float *)out[q];
     }
-    a.counters = g->stripes;  // one copy per SM: a 256-target CTA adds its counters into its SM's
+    a.counters = g->stripes;  // per-SM copies: each warp adds its counters into its SM's copy
     dim3 grid((unsigned)((g->n[0] + BX - 1) / BX), (unsigned)((g->n[1] + BY - 1) / BY),
               (unsigned)((g->n[2] + BZ - 1) / BZ));
     VelArgs<float> vn;

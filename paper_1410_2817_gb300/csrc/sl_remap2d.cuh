@@ -1,5 +1,6 @@
 // sl_remap2d.cuh -- persistent 2-D FP32 remap of the FSL step (arXiv:1410.2817) with TMA-staged
-// departure windows: one CTA per SM walks through TX x TY tiles of target (reference) nodes.
+// departure windows: each CTA walks through a static list of TX x TY tiles of target (reference)
+// nodes (the last, partial round cut into half tiles, see item2).
 //
 // Per tile (Sec. 2.2, 2.3, eq. multiZ):
 //   1. start points s = j - D_j of the tile's targets and the box of their elements floor(s);
@@ -15,7 +16,9 @@
 //      (eq. multiZ) on packed FP32x2 FMAs.  Consecutive lanes take consecutive targets of a row,
 //      so that their shared-memory reads fall in distinct banks.
 // The window of the CTA's next tile is copied while the current tile is computed (two window
-// slots); the next tile's displacements are loaded into registers one tile ahead.  Targets the
+// slots); the next tile's displacements are loaded into registers one tile ahead.  The fused
+// variant also integrates the next step's trajectories of the tile's nodes (eq. vel; the swirl's
+// two nodes of a thread at a time on packed FP32x2 arithmetic).  Targets the
 // fast path cannot finish (walk leaves the window, FP32 Newton fails or meets a nearly degenerate
 // element) take the general path of the shared tile body: walk with global reads, FP64 re-solve.
 //
@@ -746,7 +749,6 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
     __shared__ Win2 W[2];
     __shared__ int abort_flag;
     const TileArgs &a = A.t;
-    const int G = (int)gridDim.x;
     LocalCounters cnt;
     cnt.clear();
     if (threadIdx.x == 0) {
