@@ -164,13 +164,15 @@ typedef struct {
     uint8_t *status;                /* [N] 0 ok, 1 locate, 2 newton, 3 fold                          */
 } sl_remap_debug;
 
-/* Bytes of device workspace a grid needs (two displacement buffers, flags, counters, reduction
- * scratch).  Returns 0 for an invalid descriptor. */
+/* Bytes of device workspace a grid needs (two displacement buffers, flags, counters and their
+ * per-SM copies, reduction scratch; for the swirl and the deformation flow, sin(pi x) and
+ * cos(pi x) at the node coordinates).  Returns 0 for an invalid descriptor. */
 size_t sl_grid_workspace_bytes(const sl_grid_desc *desc);
 
 /* Create a grid (Sec. 2: reference mesh plus Lagrangian grid).  `dev_workspace` is caller-owned
  * device memory of at least sl_grid_workspace_bytes(desc) bytes, 256-byte aligned; the grid
- * borrows it until sl_destroy_grid.  Zeroes the counters and the displacement (synchronises). */
+ * borrows it until sl_destroy_grid.  Zeroes the counters and the displacement and fills the sin/cos
+ * tables (synchronises). */
 sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspace, size_t ws_bytes, sl_grid **out);
 sl_status sl_destroy_grid(sl_grid *grid);
 

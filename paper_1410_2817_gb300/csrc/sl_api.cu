@@ -114,7 +114,7 @@ static const char *check_desc(const sl_grid_desc *d)
 }
 
 struct Layout {
-    size_t counters, stripes, partials, moment_out, flags, flags2, D0, D1, rk, total;
+    size_t counters, stripes, trig, partials, moment_out, flags, flags2, D0, D1, rk, total;
 };
 
 static Layout layout_of(const sl_grid_desc *d)
@@ -129,6 +129,12 @@ static Layout layout_of(const sl_grid_desc *d)
     off += align256(sizeof(DevCounters));
     L.stripes = off;
     off += align256(sizeof(DevCounters) * SL_COUNTER_STRIPES);
+    L.trig = off;
+    if (d->velocity_kind == SL_VEL_SWIRL2D || d->velocity_kind == SL_VEL_DEFORM3D) {
+        long long nt = 0;
+        for (int a = 0; a < d->dim; ++a) nt += d->n[a];
+        off += align256((size_t)nt * 2 * ts);
+    }
     L.partials = off;
     off += align256(sizeof(double) * 8 * SL_MOMENT_BLOCKS);
     L.moment_out = off;
@@ -190,6 +196,15 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     g->ws_bytes = ws_bytes;
     g->counters = (DevCounters *)(g->ws + L.counters);
     g->stripes = (DevCounters *)(g->ws + L.stripes);
+    g->trig = nullptr;
+    if (desc->velocity_kind == SL_VEL_SWIRL2D || desc->velocity_kind == SL_VEL_DEFORM3D) {
+        g->trig = g->ws + L.trig;
+        long long o = 0;
+        for (int a = 0; a < 3; ++a) {
+            g->trig_off[a] = o;
+            if (a < desc->dim) o += 2 * desc->n[a];
+        }
+    }
     g->partials = (double *)(g->ws + L.partials);
     g->moment_out = (double *)(g->ws + L.moment_out);
     g->flags = (uint8_t *)(g->ws + L.flags);
@@ -209,6 +224,7 @@ extern "C" sl_status sl_create_grid(const sl_grid_desc *desc, void *dev_workspac
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ws, 0, L.total, 0);
+    if (e == cudaSuccess) e = launch_trig_tables(g, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         free(g);

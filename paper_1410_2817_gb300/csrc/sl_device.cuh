@@ -100,6 +100,9 @@ struct VelArgs {
     T ct[3 * SL_MAX_SUBSTEPS];
     T lo[3], dx[3], inv_dx[3];
     T dt;
+    // sin(pi x), cos(pi x) at the grid's node coordinates x = lo + k dx of each axis (pairs, node k
+    // at 2k), tabulated once per grid for the swirl and the deformation flow; null otherwise
+    const T *sc[3];
 };
 
 template <typename T>
@@ -443,13 +446,12 @@ __device__ __forceinline__ void trig_velocity(int kind, const T s[3], const T c[
 // (sincospi_near); the stages, times and weights are rk4_cells' own, k1 + 2 k2 + 2 k3 + k4 summed
 // left to right.
 template <typename T, int DIM>
-__device__ __forceinline__ void rk4_trig_cells(const VelArgs<T> &v, const T X[3], T out[3])
+__device__ __forceinline__ void rk4_trig_from(const VelArgs<T> &v, const T X[3], const T s0[3], const T c0[3],
+                                             T out[3])
 {
-    T s0[3] = {T(0), T(0), T(0)}, c0[3] = {T(1), T(1), T(1)}, s[3], c[3];
+    T s[3], c[3];
     T k1[3], k2[3], k3[3], k4[3];
     const T h = v.dt, hh = T(0.5) * v.dt, h6 = v.dt / T(6);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) sincospi_t(X[a], &s0[a], &c0[a]);
     trig_velocity<T, DIM>(v.kind, s0, c0, v.ct[0], k1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -470,6 +472,37 @@ __device__ __forceinline__ void rk4_trig_cells(const VelArgs<T> &v, const T X[3]
         const T sum = fma_rn_t(T(2), k3[a], fma_rn_t(T(2), k2[a], k1[a])) + k4[a];
         out[a] = mul_rn_t(mul_rn_t(h6, sum), v.inv_dx[a]);
     }
+}
+
+// rk4_trig_from with the sines and cosines of pi X evaluated here
+template <typename T, int DIM>
+__device__ __forceinline__ void rk4_trig_cells(const VelArgs<T> &v, const T X[3], T out[3])
+{
+    T s0[3] = {T(0), T(0), T(0)}, c0[3] = {T(1), T(1), T(1)};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sincospi_t(X[a], &s0[a], &c0[a]);
+    rk4_trig_from<T, DIM>(v, X, s0, c0, out);
+}
+
+// trajectory_cells for grid node j (X its position): the swirl's and the deformation flow's RK4
+// step takes sin(pi X), cos(pi X) from the grid's table (the same bits sincospi_t gives; used by
+// the trajectory launch, where it saves the FP64 path two sincospi per node; the fused launches
+// evaluate them, which measured faster there)
+template <typename T, int DIM>
+__device__ __forceinline__ void trajectory_cells_node(const VelArgs<T> &v, const T X[3], const int j[3], T out[3])
+{
+    if (v.sc[0] != nullptr && v.integrator == SL_RK4 && v.substeps == 1 &&
+        ((DIM == 2 && v.kind == SL_VEL_SWIRL2D) || (DIM == 3 && v.kind == SL_VEL_DEFORM3D))) {
+        T s0[3] = {T(0), T(0), T(0)}, c0[3] = {T(1), T(1), T(1)};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            s0[a] = __ldg(v.sc[a] + 2 * j[a]);
+            c0[a] = __ldg(v.sc[a] + 2 * j[a] + 1);
+        }
+        rk4_trig_from<T, DIM>(v, X, s0, c0, out);
+        return;
+    }
+    trajectory_cells<T, DIM>(v, X, out);
 }
 
 // ---- the swirl's RK4 step for two nodes at once -------------------------------------------------
@@ -563,12 +596,12 @@ __device__ __forceinline__ void swirl_velocity_pair(float2 sX, float2 cX, float2
 
 // rk4_trig_cells<float, 2> for the swirl at the positions (X.x, Y.x) and (X.y, Y.y): the
 // displacements in cell units, dx of the two nodes in Dx, dy in Dy
-__device__ __forceinline__ void rk4_swirl_pair(const VelArgs<float> &v, float2 X, float2 Y, float2 &Dx, float2 &Dy)
+// (s0x, c0x, s0y, c0y: the sines and cosines of pi X and pi Y of the two nodes)
+__device__ __forceinline__ void rk4_swirl_pair_from(const VelArgs<float> &v, float2 X, float2 Y, float2 s0x, float2 c0x,
+                                                    float2 s0y, float2 c0y, float2 &Dx, float2 &Dy)
 {
     const float h = v.dt, hh = 0.5f * v.dt, h6 = v.dt / 6.f;
-    float2 s0x, c0x, s0y, c0y, sx, cx, sy, cy, k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
-    sincospi_pair(X, &s0x, &c0x);
-    sincospi_pair(Y, &s0y, &c0y);
+    float2 sx, cx, sy, cy, k1x, k1y, k2x, k2y, k3x, k3y, k4x, k4y;
     swirl_velocity_pair(s0x, c0x, s0y, c0y, v.ct[0], k1x, k1y);
     sincospi_near_pair(s0x, c0x, X, hh, k1x, &sx, &cx);
     sincospi_near_pair(s0y, c0y, Y, hh, k1y, &sy, &cy);
@@ -584,6 +617,14 @@ __device__ __forceinline__ void rk4_swirl_pair(const VelArgs<float> &v, float2 X
     const float2 sumx = make_float2(ax.x + k4x.x, ax.y + k4x.y), sumy = make_float2(ay.x + k4y.x, ay.y + k4y.y);
     Dx = __fmul2_rn(__fmul2_rn(f2(h6), sumx), f2(v.inv_dx[0]));
     Dy = __fmul2_rn(__fmul2_rn(f2(h6), sumy), f2(v.inv_dx[1]));
+}
+
+__device__ __forceinline__ void rk4_swirl_pair(const VelArgs<float> &v, float2 X, float2 Y, float2 &Dx, float2 &Dy)
+{
+    float2 s0x, c0x, s0y, c0y;
+    sincospi_pair(X, &s0x, &c0x);
+    sincospi_pair(Y, &s0y, &c0y);
+    rk4_swirl_pair_from(v, X, Y, s0x, c0x, s0y, c0y, Dx, Dy);
 }
 
 template <typename T, int DIM>

@@ -17,7 +17,11 @@ struct sl_grid {
     char *ws;
     size_t ws_bytes;
     DevCounters *counters;
-    DevCounters *stripes;        // SL_COUNTER_STRIPES more copies, one per SM (kernels with many small
+    DevCounters *stripes;
+    // sin(pi x), cos(pi x) at the node coordinates of each axis (pairs; axis a at trig_off[a] in
+    // units of the dtype), for the trajectory launch of the swirl and the deformation flow
+    void *trig;
+    int64_t trig_off[3];        // SL_COUNTER_STRIPES more copies, one per SM (kernels with many small
                                  // CTAs add into their SM's copy); read together with counters
     double *partials;            // moments: SL_MOMENT_BLOCKS x 8
     double *moment_out;          // 8 doubles
@@ -75,6 +79,7 @@ struct Launch {
 };
 
 // 3-D FP32 kernels (sl_blocked3d.cu): box flags end up in `tmp`
+cudaError_t launch_trig_tables(const sl_grid *g, cudaStream_t s);
 cudaError_t launch_box_flags3d(const sl_grid *g, const void *const *in, uint8_t *flags, uint8_t *tmp, cudaStream_t s);
 cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, const uint8_t *box, double t_next,
                              double dt, bool fused, const void *const *in, void *const *out, cudaStream_t s);

@@ -56,7 +56,40 @@ VelArgs<T> make_vel_args(const sl_grid *g, double t, double dt)
         v.inv_dx[q] = (T)(1.0 / g->dx[q]);
     }
     v.dt = (T)dt;
+    if (g->trig != nullptr && sizeof(T) == g->tsize)
+        for (int q = 0; q < g->dim; ++q) v.sc[q] = (const T *)g->trig + g->trig_off[q];
     return v;
+}
+
+// sin(pi x), cos(pi x) at every node coordinate of every axis, computed by the kernels' own
+// node_position and sincospi_t (so a table entry has the bits the kernels compute)
+template <typename T>
+__global__ void __launch_bounds__(256) trig_table_kernel(VelArgs<T> v, int dim, int n0, int n1, int n2, T *tab)
+{
+    const int n[3] = {n0, n1, n2};
+    long long base = 0;
+    for (int a = 0; a < dim; ++a) {
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n[a]; k += gridDim.x * blockDim.x) {
+            T sn, cs;
+            sincospi_t(node_position(v.lo[a], k, v.dx[a]), &sn, &cs);
+            tab[base + 2 * k] = sn;
+            tab[base + 2 * k + 1] = cs;
+        }
+        base += 2LL * n[a];
+    }
+}
+
+cudaError_t launch_trig_tables(const sl_grid *g, cudaStream_t s)
+{
+    if (g->trig == nullptr) return cudaSuccess;
+    const int n1 = g->dim > 1 ? (int)g->n[1] : 0, n2 = g->dim > 2 ? (int)g->n[2] : 0;
+    if (g->dtype == SL_F64)
+        trig_table_kernel<double><<<64, 256, 0, s>>>(make_vel_args<double>(g, 0.0, 1.0), g->dim, (int)g->n[0], n1, n2,
+                                                     (double *)g->trig);
+    else
+        trig_table_kernel<float><<<64, 256, 0, s>>>(make_vel_args<float>(g, 0.0, 1.0), g->dim, (int)g->n[0], n1, n2,
+                                                    (float *)g->trig);
+    return cudaGetLastError();
 }
 
 // One block per `threads` nodes (the kernels also loop grid-stride, so any count is correct).
@@ -149,7 +182,7 @@ __global__ void __launch_bounds__(256) advect_kernel(GridArgs<T> g, VelArgs<T> v
         T X[3] = {T(0), T(0), T(0)}, d[3];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) X[a] = node_position(v.lo[a], k[a], v.dx[a]);
-        trajectory_cells<T, DIM>(v, X, d);
+        trajectory_cells_node<T, DIM>(v, X, k, d);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) D[i * ds + a] = d[a];
         if (DIM == 3) D[i * ds + 3] = T(0);

@@ -677,9 +677,10 @@ __device__ __forceinline__ void integrate_next2(const TileArgs &a, const VelArgs
             const bool ina = jxa < a.n0 && jy < ylim, inb = jxb < a.n0 && jy < ylim;
             if (!ina && !inb) continue;
             const float Y = node_position(vn.lo[1], jy, vn.dx[1]);
+            const float2 Xp = make_float2(node_position(vn.lo[0], jxa, vn.dx[0]), node_position(vn.lo[0], jxb, vn.dx[0]));
+            // (sin, cos of pi x evaluated here: reading them from the grid's table measured slower)
             float2 Dx, Dy;
-            rk4_swirl_pair(vn, make_float2(node_position(vn.lo[0], jxa, vn.dx[0]), node_position(vn.lo[0], jxb, vn.dx[0])),
-                           make_float2(Y, Y), Dx, Dy);
+            rk4_swirl_pair(vn, Xp, make_float2(Y, Y), Dx, Dy);
             const long long jj = (long long)jy * a.n0 + jxa;
             if (ina) Dn[jj] = make_float2(Dx.x, Dy.x);
             if (inb) Dn[jj + Cfg::PX] = make_float2(Dx.y, Dy.y);
