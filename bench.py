@@ -284,7 +284,7 @@ def kernel_only(args):
         if args.mode == "remap_z2":
             wl.max_order = 2
     f64 = args.mode == "step64"
-    g = sl.grid_for(wl, sl.SL_F64 if f64 else sl.SL_F32)
+    g = sl.grid_for(wl, sl.SL_F64 if f64 else sl.SL_F32, tile_config=args.tile_config)
     f = torch.tensor(wl.fields, dtype=torch.float64 if f64 else torch.float32, device="cuda")
     out = torch.empty_like(f)
     if args.mode != "nlsw":
@@ -391,7 +391,8 @@ def deform3d_leg(torch, sl, inputs, steps=5):
             out[name]["steps_compared"] = 3 + nsteps
             out[name]["time_ratio_vs_mixed"] = (tot / nsteps) / out["cubic"]["ms_per_step"]
         if name in ("cubic", "newton_f64"):
-            # sl_remap_fields alone (box flags: two passes; the blocked remap), L2 flushed
+            # sl_remap_fields alone (box flags: two passes; the staged remap, or the blocked one with
+            # FP64 inversion), L2 flushed
             g.advect(t, wl.dt)
             o = torch.empty_like(f)
             warm_flushed(flush, lambda: g.remap(f, o), 3)
@@ -409,6 +410,25 @@ def deform3d_leg(torch, sl, inputs, steps=5):
                 out[name]["remap_ms"] = remap_ms
                 g.close()
                 continue
+            # the same remap on the blocked kernel (every value gathered through L1), which the
+            # staged kernel replaces for plain remaps: identical results, timed the same way
+            gb = sl.grid_for(wl, sl.SL_F32, newton_mode=newton, tile_config=1)
+            gb.advect(t, wl.dt)
+            ob = torch.empty_like(f)
+            warm_flushed(flush, lambda: gb.remap(f, ob), 3)
+            rb = []
+            for k in range(nsteps):
+                flush.fill_(k)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                gb.remap(f, ob)
+                b.record()
+                rb.append((a, b))
+            torch.cuda.synchronize()
+            out[name]["remap_blocked_l1"] = {"remap_ms": sum(a.elapsed_time(b) for a, b in rb) / nsteps,
+                                             "identical_to_staged": bool(torch.equal(o, ob)),
+                                             "kernel": "remap_blocked3d_kernel (tile configuration 1)"}
+            gb.close()
             hbm, kind = _peaks()
             F, N3 = wl.nfields, wl.nnodes
             step_bytes, remap_bytes = N3 * 2 * F * 4, N3 * (3 * 4 + 2 * F * 4)
@@ -419,7 +439,8 @@ def deform3d_leg(torch, sl, inputs, steps=5):
                                      "unit": "GB/s", "frac": sa / hbm, "traffic": None, "peak_kind": kind,
                                      "algorithmic_bytes_per_launch": step_bytes,
                                      "bytes_rule": "2 F T per node (16 B)", "timed_over": "the leg's flushed steps"}
-            out[name]["roofline_remap"] = {"bound": "hbm", "kernel": "sl_remap_fields 3-D (three launches)",
+            out[name]["roofline_remap"] = {"bound": "hbm", "kernel": "sl_remap_fields 3-D: flags and x-OR, y/z-OR, "
+                                           "staged remap (three launches)",
                                            "achieved": ra, "peak": hbm, "unit": "GB/s", "frac": ra / hbm,
                                            "traffic": None, "peak_kind": kind,
                                            "algorithmic_bytes_per_launch": remap_bytes,
@@ -662,6 +683,8 @@ def main():
     ap.add_argument("--mode", default="full", choices=["full", "remap", "step", "step64", "remap3d", "step3d", "remap_z2", "nlsw"],
                     help="remap/step: only launch that call --steps times (for profilers); prints its timing")
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side for --mode remap/step")
+    ap.add_argument("--tile-config", type=int, default=0,
+                    help="tile configuration of the grid for --mode (3-D: 1 runs the blocked L1 kernel)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -132,7 +132,15 @@ typedef struct {
                                        per SM, 5: 32x32 pipelined (persistent, one CTA per SM
                                        staging the next tiles while it computes; 1 above 4
                                        fields) -- the shared-memory tile kernels with per-element
-                                       copies.  Batches take their own tile configuration (0..5). */
+                                       copies.  Batches take their own tile configuration (0..5).
+                                       3-D FP32 grids: 1 runs the blocked kernel, which gathers
+                                       every value through L1; any other value runs plain remaps
+                                       on the staged kernel (the field values of each 16x4x4
+                                       target block's stencils copied to shared memory during the
+                                       element search: TMA boxes inside the grid, per-element
+                                       copies across the seam) where it applies -- up to 2
+                                       fields, newton_mode other than SL_NEWTON_F64 -- and fused
+                                       steps on the blocked kernel.  Both give identical results. */
     int trajectory_substeps;        /* integrator steps per remap (Sec. 2: the Lagrangian grid may
                                        move for several time steps before the fields are
                                        interpolated back): each step of length dt integrates the

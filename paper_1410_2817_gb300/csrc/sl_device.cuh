@@ -716,12 +716,21 @@ __device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T to
     return ST_NEWTON;
 }
 
+// 3x3 determinant by the first row's cofactors.  Every product and sum is rounded explicitly (as
+// in the trilinear map below), so that the compiler cannot contract them differently in the
+// kernels that inline this: the staged and blocked 3-D kernels, fused or not, then invert every
+// element to the same bits.
 template <typename T>
 __device__ __forceinline__ T det3(T a00, T a01, T a02, T a10, T a11, T a12, T a20, T a21, T a22)
 {
-    return a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
+    const T m0 = fma_rn_t(a11, a22, -mul_rn_t(a12, a21));
+    const T m1 = fma_rn_t(a10, a22, -mul_rn_t(a12, a20));
+    const T m2 = fma_rn_t(a10, a21, -mul_rn_t(a11, a20));
+    return fma_rn_t(a02, m2, fma_rn_t(-a01, m1, mul_rn_t(a00, m0)));
 }
 
+// Newton inversion of the trilinear element map (eq. mapping1 in 3-D) from the solution of its
+// linear part; vertices P[v] relative to the target, v = x + 2 y + 4 z.
 template <typename T>
 __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T tol, T xi[3], int *iters,
                                              bool *degenerate = nullptr)
@@ -747,19 +756,25 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
     }
     T r0 = -P0[0], r1 = -P0[1], r2 = -P0[2];
     T inv = recip_t(det);
-    T s0 = det3(r0, A[0][1], A[0][2], r1, A[1][1], A[1][2], r2, A[2][1], A[2][2]) * inv;
-    T s1 = det3(A[0][0], r0, A[0][2], A[1][0], r1, A[1][2], A[2][0], r2, A[2][2]) * inv;
-    T s2 = det3(A[0][0], A[0][1], r0, A[1][0], A[1][1], r1, A[2][0], A[2][1], r2) * inv;
+    T s0 = mul_rn_t(det3(r0, A[0][1], A[0][2], r1, A[1][1], A[1][2], r2, A[2][1], A[2][2]), inv);
+    T s1 = mul_rn_t(det3(A[0][0], r0, A[0][2], A[1][0], r1, A[1][2], A[2][0], r2, A[2][2]), inv);
+    T s2 = mul_rn_t(det3(A[0][0], A[0][1], r0, A[1][0], A[1][1], r1, A[2][0], A[2][1], r2), inv);
     for (int it = 1; it <= max_iter; ++it) {
         *iters = it;
         T F[3], J[3][3];
+        const T s01 = mul_rn_t(s0, s1), s02 = mul_rn_t(s0, s2), s12 = mul_rn_t(s1, s2), s012 = mul_rn_t(s01, s2);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            F[a] = P0[a] + s0 * A[a][0] + s1 * A[a][1] + s2 * A[a][2] + s0 * s1 * E01[a] + s0 * s2 * E02[a]
-                   + s1 * s2 * E12[a] + s0 * s1 * s2 * G[a];
-            J[a][0] = A[a][0] + s1 * E01[a] + s2 * E02[a] + s1 * s2 * G[a];
-            J[a][1] = A[a][1] + s0 * E01[a] + s2 * E12[a] + s0 * s2 * G[a];
-            J[a][2] = A[a][2] + s0 * E02[a] + s1 * E12[a] + s0 * s1 * G[a];
+            T f = fma_rn_t(s0, A[a][0], P0[a]);
+            f = fma_rn_t(s1, A[a][1], f);
+            f = fma_rn_t(s2, A[a][2], f);
+            f = fma_rn_t(s01, E01[a], f);
+            f = fma_rn_t(s02, E02[a], f);
+            f = fma_rn_t(s12, E12[a], f);
+            F[a] = fma_rn_t(s012, G[a], f);
+            J[a][0] = fma_rn_t(s12, G[a], fma_rn_t(s2, E02[a], fma_rn_t(s1, E01[a], A[a][0])));
+            J[a][1] = fma_rn_t(s02, G[a], fma_rn_t(s2, E12[a], fma_rn_t(s0, E01[a], A[a][1])));
+            J[a][2] = fma_rn_t(s01, G[a], fma_rn_t(s1, E12[a], fma_rn_t(s0, E02[a], A[a][2])));
         }
         det = det3(J[0][0], J[0][1], J[0][2], J[1][0], J[1][1], J[1][2], J[2][0], J[2][1], J[2][2]);
         if (!(det > T(0))) {
@@ -769,9 +784,9 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
             return ST_FOLD;
         }
         inv = recip_t(det);
-        const T d0 = det3(F[0], J[0][1], J[0][2], F[1], J[1][1], J[1][2], F[2], J[2][1], J[2][2]) * inv;
-        const T d1 = det3(J[0][0], F[0], J[0][2], J[1][0], F[1], J[1][2], J[2][0], F[2], J[2][2]) * inv;
-        const T d2 = det3(J[0][0], J[0][1], F[0], J[1][0], J[1][1], F[1], J[2][0], J[2][1], F[2]) * inv;
+        const T d0 = mul_rn_t(det3(F[0], J[0][1], J[0][2], F[1], J[1][1], J[1][2], F[2], J[2][1], J[2][2]), inv);
+        const T d1 = mul_rn_t(det3(J[0][0], F[0], J[0][2], J[1][0], F[1], J[1][2], J[2][0], F[2], J[2][2]), inv);
+        const T d2 = mul_rn_t(det3(J[0][0], J[0][1], F[0], J[1][0], J[1][1], F[1], J[2][0], J[2][1], F[2]), inv);
         s0 -= d0;
         s1 -= d1;
         s2 -= d2;
@@ -783,7 +798,7 @@ __device__ __forceinline__ int newton_solve3(const T P[8][3], int max_iter, T to
                 T cn[3];
 #pragma unroll
                 for (int b = 0; b < 3; ++b) cn[b] = abs_t(J[0][b]) + abs_t(J[1][b]) + abs_t(J[2][b]);
-                *degenerate = det < T(SL_DEGENERATE) * (cn[0] * cn[1] * cn[2]);
+                *degenerate = det < mul_rn_t(T(SL_DEGENERATE), mul_rn_t(mul_rn_t(cn[0], cn[1]), cn[2]));
             }
             return ST_OK;
         }

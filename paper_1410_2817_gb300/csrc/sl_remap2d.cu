@@ -1,5 +1,6 @@
 // sl_remap2d.cu -- launchers of the persistent 2-D FP32 remap with TMA-staged windows
-// (sl_remap2d.cuh): tensor maps of the field planes and the displacement, one CTA (or two) per SM.
+// (sl_remap2d.cuh): tensor maps of the field planes and the displacement, one CTA (or two) per SM;
+// the tensor-map encoder shared with the staged 3-D kernel.
 #include <mutex>
 #include <string.h>
 
@@ -25,19 +26,34 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
+bool encode_tensor_f32(CUtensorMap *m, const void *base, int rank, const unsigned long long *dims,
+                       const unsigned long long *strides, const unsigned *box)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || rank < 2 || rank > 3 || ((uintptr_t)base & 15u) != 0 || (box[0] * 4u) % 16u != 0) return false;
+    cuuint64_t d[3], st[2];
+    cuuint32_t b[3], es[3];
+    for (int k = 0; k < rank; ++k) {
+        d[k] = dims[k];
+        b[k] = box[k];
+        es[k] = 1;
+        if (k + 1 < rank) {
+            if (strides[k] % 16 != 0) return false;
+            st[k] = strides[k];
+        }
+    }
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d, st, b, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // a FP32 matrix of `w` x `h` values, rows `w` values apart, copied in boxes of bw x bh
 static bool encode_f32(CUtensorMap *m, const void *base, unsigned long long w, unsigned long long h, unsigned bw,
                        unsigned bh)
 {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn || ((uintptr_t)base & 15u) != 0 || (w * 4) % 16 != 0) return false;
-    const cuuint64_t dims[2] = {w, h};
-    const cuuint64_t strides[1] = {w * 4};
-    const cuuint32_t boxd[2] = {bw, bh};
-    const cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, boxd, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const unsigned long long dims[2] = {w, h}, strides[1] = {w * 4};
+    const unsigned box[2] = {bw, bh};
+    return encode_tensor_f32(m, base, 2, dims, strides, box);
 }
 
 template <class Cfg, int NF, bool FUSED>

@@ -23,6 +23,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "sl_async.cuh"
 #include "sl_internal.h"
 
 namespace {
@@ -66,15 +67,6 @@ __device__ __forceinline__ long long gidx(int x, int y, int n0, int n1)
 {
     return (long long)wrap_idx(y, n1) * n0 + wrap_idx(x, n0);
 }
-
-// asynchronous global -> shared copies (LDGSTS); a CTA issues its whole window, then waits once
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src)
-{
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(gmem_src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // row of flat index q in a region `width` wide: (q + 0.5) / width in FP32 is exact enough to
 // floor correctly for q, width < 2^11 (the fractional part stays >= 0.5 / width)

@@ -1,13 +1,13 @@
 // sl_tiled.cu -- dispatch of the FP32 production kernels: 2-D grids go to the persistent kernel with
 // TMA-staged windows (sl_remap2d.cuh; tile configurations 0, 6, 7, up to 3 fields, analytic
 // velocities) or to the shared-memory tiled kernels (sl_tile2d.cuh, one translation unit per tile
-// configuration; the quintic Z-spline to sl_tiled_z2.cu), 3-D grids to the blocked kernels
-// (sl_blocked3d.cu, cubic and linear only).
+// configuration; the quintic Z-spline to sl_tiled_z2.cu), 3-D grids to the staged or blocked
+// kernels (sl_blocked3d.cu, cubic and linear only).
 #include <string.h>
 
 #include "sl_internal.h"
 
-// 2-D: one tiled launch; 3-D: flags with the x-OR, the y/z-OR, one blocked launch
+// 2-D: one tiled launch; 3-D: flags with the x-OR, the y/z-OR, one staged or blocked launch
 int tiled_kernels_per_call(const sl_grid *g) { return g->dim == 2 ? 1 : 3; }
 
 template <typename T>
@@ -18,7 +18,8 @@ bool Launch<T>::tiled_supported(const sl_grid *g)
     // an FP64 inversion of every target runs on the plain kernels
     if (g->dim == 2 && g->desc.newton_mode == SL_NEWTON_F64) return false;
     if (g->desc.max_order > 1) return g->dim == 2 && tiled2d_smem_bytes_z2(g->nfields) <= 200 * 1024;
-    if (g->dim == 3) return g->N < (1LL << 31);  // the blocked kernel forms 32-bit node offsets
+    // the 3-D kernels form 32-bit node offsets; their blocks are at least 4 rows and planes deep
+    if (g->dim == 3) return g->N < (1LL << 31) && (g->n[1] + 3) / 4 <= 65535 && (g->n[2] + 3) / 4 <= 65535;
     const int c = g->desc.tile_config;
     const size_t smem = c == 2   ? tiled2d_smem_bytes_cfgb(g->nfields)
                         : c == 3 ? tiled2d_smem_bytes_cfgc(g->nfields)
