@@ -345,7 +345,8 @@ def batched_leg(torch, sl, inputs, steps=50, tile_config=None, max_order=1):
 
 def deform3d_leg(torch, sl, inputs, steps=5):
     """3-D 256^3 deformation flow (T = 3, dt = 0.03), two fields, FP32 bulk with FP64 re-solves of
-    degenerate elements: `steps` full steps through sl_step, L2 flushed before each; the same steps
+    degenerate elements: `steps` full steps through sl_step_out (input and result planes swap each
+    step, as in the headline: no copy back), L2 flushed before each; the same steps
     with every target's element map inverted in FP64 (SL_NEWTON_F64 on the blocked kernel), with the
     largest difference of its fields from the mixed run's; and the quintic Z-spline (plain kernels:
     6 x 6 x 6 taps per field)."""
@@ -355,28 +356,28 @@ def deform3d_leg(torch, sl, inputs, steps=5):
         wl = inputs.workload_deform3d(256, steps=nsteps)
         wl.max_order = mo
         g = sl.grid_for(wl, sl.SL_F32, newton_mode=newton)
-        f = torch.tensor(wl.fields, dtype=torch.float32, device="cuda")
-        s = torch.empty_like(f)
+        bufs = [torch.tensor(wl.fields, dtype=torch.float32, device="cuda")]
+        bufs.append(torch.empty_like(bufs[0]))  # bufs[0]: the current fields
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-        g.step(f, s, 0.0, wl.dt, 1)
         ms = []
-        tt = [wl.dt]
+        tt = [0.0]
 
         def one():
-            g.step(f, s, tt[0], wl.dt, 1)
+            g.step_out(bufs[0], bufs[1], tt[0], wl.dt, 1)
+            bufs.reverse()
             tt[0] += wl.dt
 
+        one()
         warm_flushed(flush, one, 2)
-        t = tt[0]
         for k in range(nsteps):
             flush.fill_(k)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            g.step(f, s, t, wl.dt, 1)
+            one()
             b.record()
             ms.append((a, b))
-            t += wl.dt
         torch.cuda.synchronize()
+        f, t = bufs[0], tt[0]
         tot = sum(a.elapsed_time(b) for a, b in ms)
         out[name] = {"workload": f"deform3d 256^3, 2 fields, FP32, max_order {mo}",
                      "value": wl.nnodes * nsteps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / nsteps}

@@ -672,20 +672,31 @@ def test_blocked3d_matches_generic_f32(sl, orc, case):
     assert diags["tiled"]["targets"] == int(np.prod(n))
 
 
+@pytest.mark.parametrize("tile_config", [0, 1])
 @pytest.mark.parametrize("newton_mode", ["mixed", "f64"])
-@pytest.mark.parametrize("case", ["deform3d_32", "ragged3d"])
-def test_blocked3d_f32_per_target(sl, orc, case, newton_mode):
-    """The blocked 3-D FP32 remap, target by target against the FP64 oracle on the same FP32
-    displacement and fields: each value within 2e-6 of the oracle's interpolation in the oracle's
-    element and order, or -- within FP32 rounding of a face or of a limiter threshold -- in the
-    neighbouring element or with the other order.  Both inversions: FP32 with FP64 re-solves of
-    failed or degenerate targets (mixed), and FP64 for every target (no re-solve is counted)."""
+@pytest.mark.parametrize("case", ["deform3d_32", "deform3d_64x48x40", "ragged3d"])
+def test_blocked3d_f32_per_target(sl, orc, case, newton_mode, tile_config):
+    """The 3-D FP32 remap, target by target against the FP64 oracle on the same FP32 displacement
+    and fields: each value within 2e-6 of the oracle's interpolation in the oracle's element and
+    order, or -- within FP32 rounding of a face or of a limiter threshold -- in the neighbouring
+    element or with the other order.  Both inversions: FP32 with FP64 re-solves of failed or
+    degenerate targets (mixed), and FP64 for every target (no re-solve is counted); both kernels:
+    the staged one (tile configuration 0, plain remaps of up to 2 fields in FP32 inversion; the
+    64x48x40 grid copies two thirds of its windows by TMA boxes and the rest element by element
+    across the seam) and the blocked one (tile configuration 1)."""
     from tests import tiecheck
     rng = np.random.default_rng(33)
     if case == "deform3d_32":
         n = (32, 32, 32)
         og = _og(orc, 3, n, 2, velocity="deform3d", params=[3.0])
         D, h = orc.advect(og, 0.4, 0.03), inputs.deform3d_fields(32)
+    elif case == "deform3d_64x48x40":
+        n = (64, 48, 40)
+        og = _og(orc, 3, n, 2, velocity="deform3d", params=[3.0])
+        D = orc.advect(og, 0.7, 0.03)
+        x, y, z = inputs.node_coords(n)
+        h = np.stack([np.exp(-((x - 0.4) ** 2 + (y - 0.5) ** 2 + (z - 0.45) ** 2) / 0.02),
+                      ((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2 <= 0.09).astype(np.float64)])
     else:
         n = (19, 13, 11)
         D = inputs.smooth_displacement(n, amplitude=0.3, seed=8, shift=(1.6, -2.2, 0.7))
@@ -694,7 +705,8 @@ def test_blocked3d_f32_per_target(sl, orc, case, newton_mode):
     D32, h32 = np.asarray(D, dtype=np.float32), np.asarray(h, dtype=np.float32)
     nf = h32.shape[0]
     nm = sl.SL_NEWTON_MIXED if newton_mode == "mixed" else sl.SL_NEWTON_F64
-    g = _gpu_grid(sl, 3, n, nf, sl.SL_F32, start="backward", kernel=sl.SL_KERNEL_TILED, newton_mode=nm)
+    g = _gpu_grid(sl, 3, n, nf, sl.SL_F32, start="backward", kernel=sl.SL_KERNEL_TILED, newton_mode=nm,
+                  tile_config=tile_config)
     hin = torch.tensor(h32, device=DEV)
     hout = torch.empty_like(hin)
     g.set_displacement(torch.tensor(D32, device=DEV))
