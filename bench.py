@@ -43,7 +43,7 @@ FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at 1024^2 (3 fields) of the fused step
 # kernel (the headline's only launch) and of the plain remap kernel (sl_remap_fields), from the ncu
 # captures summarised in profiles/; valid only for the kernel source they were taken on.
-NCU_TRAFFIC = {"step_bytes_per_launch": 21094400, "remap_bytes_per_launch": 21047296, "source_sha": "b7383a2c01e25f68"}
+NCU_TRAFFIC = {"step_bytes_per_launch": 21092096, "remap_bytes_per_launch": 21047552, "source_sha": "225fdf09af7ebb0e"}
 
 
 def warm_flushed(flush, step, n=3):

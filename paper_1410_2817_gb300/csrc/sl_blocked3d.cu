@@ -488,8 +488,8 @@ __global__ void __launch_bounds__(NT3, 4) remap_blocked3d_kernel(const Blocked3A
 // blocked kernel).  Each target then waits for the copy and sums its taps from shared memory (from
 // global memory where its stencil leaves the window; the whole block when its window exceeds the
 // capacity).  Plain remaps only: a fused step's launch, which also integrates the next
-// trajectories, measured faster on the blocked kernel.  The deformation flows' blocks need ~3.5 window nodes per target against the 64
-// tap values per field that a target reads.
+// trajectories, measured faster on the blocked kernel.  On the deformation flows a block's window
+// holds ~8 nodes per target and field, against the 64 tap values per field a target reads.
 // window capacity in nodes per field plane (x a multiple of 4 nodes: the box copies' 16-byte rule)
 constexpr int HWX = 28, HWY = 12, HWZ = 12;
 constexpr int HPLANE = HWX * HWY * HWZ;  // floats per field window (a multiple of 32: planes stay 128-byte aligned)

@@ -718,8 +718,8 @@ __device__ __forceinline__ int newton_solve2(const T P[8][3], int max_iter, T to
 
 // 3x3 determinant by the first row's cofactors.  Every product and sum is rounded explicitly (as
 // in the trilinear map below), so that the compiler cannot contract them differently in the
-// kernels that inline this: the staged and blocked 3-D kernels, fused or not, then invert every
-// element to the same bits.
+// kernels that inline this: the staged and the blocked 3-D kernels, the latter fused or not, then
+// invert every element to the same bits.
 template <typename T>
 __device__ __forceinline__ T det3(T a00, T a01, T a02, T a10, T a11, T a12, T a20, T a21, T a22)
 {
@@ -965,7 +965,7 @@ __device__ __forceinline__ void flush_counters(const LocalCounters &c, DevCounte
 // Per-warp flush with no block barrier (a barrier at the end of a block costs its early warps the
 // wait for its slowest target): the warp's sums and maxima go straight to global memory from lane
 // 0, the rare counters only where the warp met one.  For kernels whose counters see few concurrent
-// adders (the blocked 3-D kernel adds into per-SM copies).
+// adders (the 3-D kernels add into per-SM copies).
 __device__ __forceinline__ void flush_counters_warp(const LocalCounters &c, DevCounters *g)
 {
     if (g == nullptr) return;

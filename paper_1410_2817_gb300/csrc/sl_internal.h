@@ -78,7 +78,8 @@ struct Launch {
                                   const void *const *in, void *const *out, cudaStream_t s);
 };
 
-// 3-D FP32 kernels (sl_blocked3d.cu): box flags end up in `tmp`
+// 3-D FP32 kernels (sl_blocked3d.cu): box flags end up in `tmp`; launch_blocked3d runs a plain
+// remap on the staged kernel where it applies, a fused step (and the rest) on the blocked one
 cudaError_t launch_trig_tables(const sl_grid *g, cudaStream_t s);
 cudaError_t launch_box_flags3d(const sl_grid *g, const void *const *in, uint8_t *flags, uint8_t *tmp, cudaStream_t s);
 cudaError_t launch_blocked3d(const sl_grid *g, const void *D, void *D_next, const uint8_t *box, double t_next,
