@@ -148,7 +148,7 @@ def _max_over_ranks(dist, torch, value: float) -> float:
 
 
 def cpu_baseline(budget_s: float = 10.0, steps_max: int = 400):
-    """The oracle (as it stands) on the GPU machine's host cores: whole 1024^2 steps until about
+    """The oracle (as it stands) on the host cores next to the GPU: whole 1024^2 steps until about
     `budget_s` seconds of CPU work are spent (at least one step).  Its result also serves as the
     reference of the FP32 production path's accuracy: the same number of FP32 steps from the same
     fields through sl_step, compared field by field (relative L1 and Linf) and in the moments
